@@ -1,0 +1,218 @@
+/*
+ * pic.h -- C ABI of the GB300-native explicit relativistic particle-in-cell
+ * step (libpic).
+ *
+ * The library advances one or many independent periodic 3D boxes through the
+ * PIC cycle that Zenker et al. run on PIConGPU ("Performance-Portable
+ * Many-Core Plasma Simulations", Sec. 2.1 and Sec. 4): field gather to the
+ * particles, Boris push, charge-conserving Esirkepov current deposition, Yee
+ * FDTD field update, with the particles kept in supercell-sorted frames
+ * (Sec. 2.1: cells are grouped into supercells; particles live in frames of
+ * as many slots as a supercell has cells, one list of frames per supercell).
+ *
+ * Units are normalised: c = 1, eps0 = mu0 = 1; dB/dt = -curl E and
+ * dE/dt = curl B - J; momenta are u = gamma v; positions are global
+ * coordinates in cell units, x in [0, N) per axis.  A macro-particle of
+ * weight w and charge q carries the charge density q w S / (dx dy dz).
+ * The Yee staggering is Ex(i+1/2, j, k), Ey(i, j+1/2, k), Ez(i, j, k+1/2),
+ * Bx(i, j+1/2, k+1/2), By(i+1/2, j, k+1/2), Bz(i+1/2, j+1/2, k); J sits with
+ * E, the charge density at the nodes.  Step order (leapfrog, B split in two
+ * halves so B is known at integer time): gather E^n, B^n; Boris
+ * u^{n-1/2} -> u^{n+1/2}; move; Esirkepov J^{n+1/2}; B^{n+1/2} = B^n -
+ * dt/2 curl E^n; E^{n+1} = E^n + dt (curl B^{n+1/2} - J^{n+1/2});
+ * B^{n+1} = B^{n+1/2} - dt/2 curl E^{n+1}.
+ *
+ * Threading: a context is used from one host thread at a time.  All device
+ * work of a context runs on the stream given in pic_options (or the legacy
+ * default stream when it is NULL).
+ *
+ * Errors: every call returns a pic_status and never aborts, throws or exits.
+ * After any error other than PIC_ERR_ARG the context is poisoned: every later
+ * call except pic_last_error and pic_destroy returns PIC_ERR_STATE.
+ */
+#ifndef PIC_H
+#define PIC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pic_ctx pic_ctx; /* opaque; owned by the library */
+
+typedef enum {
+    PIC_OK = 0,
+    PIC_ERR_ARG = 1,        /* bad argument: null pointer, bad size or index; ctx unchanged */
+    PIC_ERR_CFL = 2,        /* dt too large: c dt must be below dx_d / 2 on every axis */
+    PIC_ERR_OOM = 3,        /* the device allocator returned NULL */
+    PIC_ERR_CUDA = 4,       /* a CUDA runtime call failed (message in pic_last_error) */
+    PIC_ERR_FRAME_POOL = 5, /* the frame pool ran out of free frames during a step */
+    PIC_ERR_TIMEOUT = 6,    /* a bounded device-side wait gave up */
+    PIC_ERR_STATE = 7,      /* the context is poisoned by an earlier error */
+    PIC_ERR_CAPACITY = 8,   /* the per-step buffer of particles changing supercell overflowed */
+    PIC_ERR_PARTICLE = 9    /* a particle produced a non-finite momentum or position */
+} pic_status;
+
+/* One periodic box of nx x ny x nz cells (each a multiple of the supercell
+ * edge on that axis when the mixed form is used). */
+typedef struct {
+    int32_t nx, ny, nz;
+} pic_grid;
+
+/* One species: charge and mass in units of e and m_e (electron: -1, 1);
+ * shape 1 = cloud-in-cell (linear), 2 = triangular-shaped cloud (quadratic
+ * spline, the TSC of Sec. 4); mobile = 0 freezes the species (it still
+ * counts in the charge density and the diagnostics, and deposits no current). */
+typedef struct {
+    double charge, mass;
+    int32_t shape;
+    int32_t mobile;
+} pic_species;
+
+/* Precision forms. */
+enum {
+    PIC_PRECISION_FP64_PLAIN = 0, /* FP64 absolute positions and fields, global atomics, no sort */
+    PIC_PRECISION_MIXED = 1       /* int32 cell + FP32 offset particles in supercell frames, FP32 fields */
+};
+
+/* Field selectors for pic_write_fields / pic_read_fields. */
+enum { PIC_FIELD_E = 0, PIC_FIELD_B = 1, PIC_FIELD_J = 2, PIC_FIELD_RHO = 3 };
+
+typedef struct {
+    int32_t precision;      /* PIC_PRECISION_* */
+    int32_t sc[3];          /* supercell edge in cells (mixed form); 0,0,0 = 4 x 4 x 4 */
+    int32_t threads_per_sc; /* CUDA threads per supercell work item (mixed form); 0 = cells per supercell */
+    int32_t track_ids;      /* nonzero: carry a particle id (load order) through the frames */
+    int32_t use_graph;      /* nonzero: pic_step replays a captured CUDA graph of one step */
+    int32_t reserved;
+    int64_t pool_frames;    /* frame-pool capacity (mixed); 0 = sized at the first step from the load */
+    int64_t move_capacity;  /* capacity of the per-step buffer of particles changing supercell; 0 = auto */
+    /* Device allocator.  Both NULL: cudaMalloc / cudaFree.  Otherwise every
+     * device buffer of the context comes from dev_alloc(bytes, alloc_ud) (it
+     * must return memory usable on `stream`, 256-byte aligned, or NULL) and
+     * goes back through dev_free(ptr, alloc_ud) in pic_destroy. */
+    void* (*dev_alloc)(size_t bytes, void* alloc_ud);
+    void (*dev_free)(void* ptr, void* alloc_ud);
+    void* alloc_ud;
+    void* stream;           /* cudaStream_t for all device work; NULL = legacy default stream */
+} pic_options;
+
+/*
+ * pic_create -- set up nboxes independent periodic boxes that share the cell
+ * size dx[3], the time step dt and the species table (Sec. 2.1: the
+ * simulation domain is a grid of cells grouped into supercells).
+ *   grids[nboxes]   box sizes (host array, copied).
+ *   dx[3]           cell edge per axis (host array, copied), > 0.
+ *   dt              time step; rejected with PIC_ERR_CFL unless dt < dx_d / 2
+ *                   on every axis (so no particle crosses more than half a
+ *                   cell per step) and dt is below the 3D Yee Courant limit.
+ *   sp[nspecies]    species table (host array, copied); 1 <= nspecies <= 8.
+ *   opt             options (host, copied); NULL = all defaults.
+ *   out             receives the new context.
+ * Fields start at zero, boxes start empty.  On any error *out is NULL and
+ * everything allocated is released.
+ */
+pic_status pic_create(const pic_grid* grids, int32_t nboxes, const double dx[3], double dt,
+                      const pic_species* sp, int32_t nspecies, const pic_options* opt,
+                      pic_ctx** out);
+
+/*
+ * pic_set_background -- a fixed, uniform charge density rho_bg for box `box`
+ * (a neutralising background).  It adds to the charge density of the
+ * diagnostics and carries no current.
+ */
+pic_status pic_set_background(pic_ctx* ctx, int32_t box, double rho_bg);
+
+/*
+ * pic_load_particles -- append n particles of species `species` to box `box`.
+ *   x[n*3]  global positions in cell units (host, FP64); wrapped
+ *           periodically into [0, N) on load.
+ *   u[n*3]  momenta u = gamma v, taken as u^{n-1/2} of the next step.
+ *   w[n]    weights, or NULL for all ones.
+ * All host arrays are read, not kept.  With track_ids the particles get ids
+ * equal to their running load index within (box, species).  Returns
+ * PIC_ERR_ARG for non-finite input.
+ */
+pic_status pic_load_particles(pic_ctx* ctx, int32_t box, int32_t species, int64_t n,
+                              const double* x, const double* u, const double* w);
+
+/*
+ * pic_write_fields -- overwrite field `which` (PIC_FIELD_E or PIC_FIELD_B) of
+ * box `box` from f[3*nz*ny*nx] (host, FP64, component-major, x fastest).
+ */
+pic_status pic_write_fields(pic_ctx* ctx, int32_t box, int32_t which, const double* f);
+
+/*
+ * pic_step -- advance every box by nsteps full PIC cycles (step order above).
+ * Blocks until the device finished, then checks the device status word:
+ * PIC_ERR_FRAME_POOL, PIC_ERR_CAPACITY, PIC_ERR_PARTICLE or PIC_ERR_TIMEOUT
+ * report a condition raised by a kernel.
+ */
+pic_status pic_step(pic_ctx* ctx, int32_t nsteps);
+
+/*
+ * pic_step_async -- as pic_step but returns once the work is enqueued on the
+ * context's stream; device conditions surface at the next pic_sync.
+ */
+pic_status pic_step_async(pic_ctx* ctx, int32_t nsteps);
+
+/* pic_sync -- wait for the context's stream and check the device status word. */
+pic_status pic_sync(pic_ctx* ctx);
+
+/*
+ * pic_read_fields -- copy field `which` of box `box` into out[3*nz*ny*nx]
+ * (PIC_FIELD_E, _B, _J) or out[nz*ny*nx] (PIC_FIELD_RHO, the charge density
+ * at the nodes including the background), host, FP64, x fastest.  J is the
+ * current of the last step (J^{n+1/2}).
+ */
+pic_status pic_read_fields(pic_ctx* ctx, int32_t box, int32_t which, double* out);
+
+/*
+ * pic_count_particles -- number of particles of (box, species) into *n_out.
+ */
+pic_status pic_count_particles(pic_ctx* ctx, int32_t box, int32_t species, int64_t* n_out);
+
+/*
+ * pic_read_particles -- copy the particles of (box, species) to host FP64
+ * arrays: x[cap*3] global positions in cell units, u[cap*3], w[cap]; id[cap]
+ * (optional, NULL to skip; requires track_ids).  Any of x, u, w may be NULL
+ * to skip it.  The order is unspecified (frames reorder particles).  *n_out
+ * receives the count; PIC_ERR_ARG if it exceeds cap (nothing is copied).
+ */
+pic_status pic_read_particles(pic_ctx* ctx, int32_t box, int32_t species, int64_t cap,
+                              double* x, double* u, double* w, int64_t* id, int64_t* n_out);
+
+/*
+ * pic_diagnostics -- FP64 reductions of box `box` into out[4]:
+ *   out[0] field energy   sum over cells of (E^2 + B^2)/2 * dx dy dz,
+ *   out[1] kinetic energy sum over particles of w m (gamma - 1),
+ *   out[2] total charge   sum of q w plus rho_bg * volume,
+ *   out[3] max over nodes of |div E - rho| (Gauss's law residual).
+ * Computed on the device in FP64 from the current state.
+ */
+pic_status pic_diagnostics(pic_ctx* ctx, int32_t box, double out[4]);
+
+/*
+ * pic_stage_times -- device time in milliseconds of each stage of the last
+ * nsteps pic_step calls since pic_stage_timing(ctx, 1) (CUDA events on the
+ * context's stream): ms[0] push+deposit, ms[1] frame maintenance,
+ * ms[2] Yee update (with the J fold), ms[3] whole step; *nsteps_out
+ * receives the number of steps summed.  Timing adds events between stages;
+ * it is off by default.
+ */
+pic_status pic_stage_timing(pic_ctx* ctx, int32_t enable);
+pic_status pic_stage_times(pic_ctx* ctx, double ms[4], int64_t* nsteps_out);
+
+/* pic_last_error -- human-readable message of the last error (never NULL). */
+const char* pic_last_error(const pic_ctx* ctx);
+
+/* pic_destroy -- release every resource of the context; NULL is a no-op. */
+void pic_destroy(pic_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PIC_H */

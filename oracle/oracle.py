@@ -1,0 +1,261 @@
+"""FP64 CPU oracle of one explicit relativistic PIC step -- TEST INFRASTRUCTURE.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this module.  The product library never does: it
+shares no code with the oracle, and the oracle shares none with it.
+
+The arithmetic lives in ``pic_oracle.c`` (plain loops, FP64, one function per
+algorithm the paper names in Sec. 4: Yee field solver, product-of-1D-weights
+field gather, Boris pusher, Esirkepov current deposition, CIC / TSC shapes).
+This file builds that C file with gcc, loads it with ctypes and strings the
+functions together in the step order of the leapfrog cycle (Sec. 2.1 and
+Sec. 4):
+
+    gather E^n, B^n -> Boris -> move -> Esirkepov J^{n+1/2}
+    -> B^{n+1/2} = B^n - dt/2 curl E^n -> E^{n+1} = E^n + dt (curl B - J)
+    -> B^{n+1} = B^{n+1/2} - dt/2 curl E^{n+1}
+
+Arrays: fields are (3, nz, ny, nx) float64, x fastest; particle positions
+are (n, 3) global coordinates in cell units in [0, N); momenta u = gamma v
+are (n, 3); weights (n,).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "pic_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "libpic_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+ORC_OK = 0
+ORC_ERR_ARG = 1
+ORC_ERR_DISPLACEMENT = 2
+
+
+class _Grid(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int64),
+        ("ny", ctypes.c_int64),
+        ("nz", ctypes.c_int64),
+        ("dx", ctypes.c_double),
+        ("dy", ctypes.c_double),
+        ("dz", ctypes.c_double),
+    ]
+
+
+def build(force: bool = False) -> str:
+    """Compile pic_oracle.c into a shared library (gcc, -O2, no fast-math and
+    no FMA contraction, so that x86 and Arm hosts give identical results)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+           "-fno-fast-math", "-Wall", "-Wextra", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = build()
+            L = ctypes.CDLL(path)
+            dp = ctypes.POINTER(ctypes.c_double)
+            gp = ctypes.POINTER(_Grid)
+            L.orc_shape.argtypes = [ctypes.c_int, ctypes.c_double]
+            L.orc_shape.restype = ctypes.c_double
+            L.orc_gather.argtypes = [gp, ctypes.c_int, dp, dp, dp, dp, dp]
+            L.orc_gather.restype = None
+            L.orc_boris.argtypes = [ctypes.c_double] * 3 + [dp, dp, dp]
+            L.orc_boris.restype = None
+            L.orc_deposit_esirkepov.argtypes = [gp, ctypes.c_int, ctypes.c_double,
+                                                ctypes.c_double, dp, dp, dp]
+            L.orc_deposit_esirkepov.restype = ctypes.c_int
+            L.orc_push_deposit.argtypes = [gp, ctypes.c_double, ctypes.c_int, ctypes.c_double,
+                                           ctypes.c_double, dp, dp, dp, ctypes.c_int64,
+                                           dp, dp, dp]
+            L.orc_push_deposit.restype = ctypes.c_int
+            L.orc_yee_b.argtypes = [gp, ctypes.c_double, dp, dp]
+            L.orc_yee_b.restype = None
+            L.orc_yee_e.argtypes = [gp, ctypes.c_double, dp, dp, dp]
+            L.orc_yee_e.restype = None
+            L.orc_yee_step.argtypes = [gp, ctypes.c_double, dp, dp, dp]
+            L.orc_yee_step.restype = None
+            L.orc_deposit_rho.argtypes = [gp, ctypes.c_int, ctypes.c_double, ctypes.c_int64,
+                                          dp, dp, dp]
+            L.orc_deposit_rho.restype = None
+            L.orc_div_e.argtypes = [gp, dp, dp]
+            L.orc_div_e.restype = None
+            L.orc_field_energy.argtypes = [gp, dp, dp]
+            L.orc_field_energy.restype = ctypes.c_double
+            L.orc_kinetic_energy.argtypes = [ctypes.c_double, ctypes.c_int64, dp, dp]
+            L.orc_kinetic_energy.restype = ctypes.c_double
+            _lib = L
+    return _lib
+
+
+def _ptr(a: np.ndarray | None):
+    if a is None:
+        return None
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"], "oracle wants C-contiguous float64"
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _f64(a, shape=None):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+    if shape is not None:
+        a = a.reshape(shape)
+    return a
+
+
+def grid(nx, ny, nz, dx=(1.0, 1.0, 1.0)) -> _Grid:
+    return _Grid(int(nx), int(ny), int(nz), float(dx[0]), float(dx[1]), float(dx[2]))
+
+
+# ---------------------------------------------------------------- primitives
+
+def shape(order: int, d: float) -> float:
+    """1D assignment function S(d): order 1 = CIC, 2 = TSC (Hockney & Eastwood)."""
+    return lib().orc_shape(int(order), float(d))
+
+
+def gather(g: _Grid, order: int, E: np.ndarray, B: np.ndarray, x) -> tuple[np.ndarray, np.ndarray]:
+    """E and B interpolated to one position x (3,) in cell units."""
+    xp = _f64(x, (3,))
+    Ep = np.zeros(3)
+    Bp = np.zeros(3)
+    lib().orc_gather(ctypes.byref(g), int(order), _ptr(E), _ptr(B), _ptr(xp), _ptr(Ep), _ptr(Bp))
+    return Ep, Bp
+
+
+def boris(q: float, m: float, dt: float, E, B, u) -> np.ndarray:
+    """One relativistic Boris update of u = gamma v; returns the new u."""
+    E = _f64(E, (3,))
+    B = _f64(B, (3,))
+    uu = _f64(u, (3,)).copy()
+    lib().orc_boris(float(q), float(m), float(dt), _ptr(E), _ptr(B), _ptr(uu))
+    return uu
+
+
+def deposit_esirkepov(g: _Grid, order: int, qw: float, dt: float, x0, x1, J: np.ndarray) -> None:
+    """Add one particle's Esirkepov current for the move x0 -> x1 into J."""
+    a = _f64(x0, (3,))
+    b = _f64(x1, (3,))
+    rc = lib().orc_deposit_esirkepov(ctypes.byref(g), int(order), float(qw), float(dt),
+                                     _ptr(a), _ptr(b), _ptr(J))
+    if rc != ORC_OK:
+        raise ValueError(f"oracle Esirkepov deposit rejected the move (code {rc})")
+
+
+def deposit_rho(g: _Grid, order: int, q: float, x: np.ndarray, w: np.ndarray | None,
+                rho: np.ndarray) -> None:
+    lib().orc_deposit_rho(ctypes.byref(g), int(order), float(q), int(x.shape[0]), _ptr(x),
+                          _ptr(w), _ptr(rho))
+
+
+def div_e(g: _Grid, E: np.ndarray) -> np.ndarray:
+    out = np.zeros((g.nz, g.ny, g.nx))
+    lib().orc_div_e(ctypes.byref(g), _ptr(E), _ptr(out))
+    return out
+
+
+def yee_b(g: _Grid, tau: float, E: np.ndarray, B: np.ndarray) -> None:
+    lib().orc_yee_b(ctypes.byref(g), float(tau), _ptr(E), _ptr(B))
+
+
+def yee_e(g: _Grid, dt: float, E: np.ndarray, B: np.ndarray, J: np.ndarray) -> None:
+    lib().orc_yee_e(ctypes.byref(g), float(dt), _ptr(E), _ptr(B), _ptr(J))
+
+
+# ---------------------------------------------------------------- full state
+
+@dataclass
+class Species:
+    """One macro-particle species: charge q, mass m (in e and m_e), shape
+    order (1 = CIC, 2 = TSC), mobile flag, and its particle arrays."""
+    q: float
+    m: float
+    order: int
+    x: np.ndarray
+    u: np.ndarray
+    w: np.ndarray | None = None
+    mobile: bool = True
+
+    def __post_init__(self):
+        self.x = _f64(self.x).reshape(-1, 3).copy()
+        self.u = _f64(self.u).reshape(-1, 3).copy()
+        if self.w is not None:
+            self.w = _f64(self.w).reshape(-1).copy()
+
+
+@dataclass
+class State:
+    """One periodic box: fields, species, and a fixed uniform background
+    charge density rho_bg (it adds to rho and carries no current)."""
+    nx: int
+    ny: int
+    nz: int
+    dt: float
+    dx: tuple = (1.0, 1.0, 1.0)
+    E: np.ndarray | None = None
+    B: np.ndarray | None = None
+    J: np.ndarray | None = None
+    species: list = field(default_factory=list)
+    rho_bg: float = 0.0
+
+    def __post_init__(self):
+        shp = (3, self.nz, self.ny, self.nx)
+        self.E = np.zeros(shp) if self.E is None else _f64(self.E, shp).copy()
+        self.B = np.zeros(shp) if self.B is None else _f64(self.B, shp).copy()
+        self.J = np.zeros(shp) if self.J is None else _f64(self.J, shp).copy()
+        self.g = grid(self.nx, self.ny, self.nz, self.dx)
+
+    def step(self, nsteps: int = 1) -> None:
+        """Advance nsteps full PIC cycles in the order of the module docstring."""
+        L = lib()
+        for _ in range(nsteps):
+            self.J[...] = 0.0
+            for sp in self.species:
+                if not sp.mobile:
+                    continue
+                rc = L.orc_push_deposit(ctypes.byref(self.g), float(self.dt), int(sp.order),
+                                        float(sp.q), float(sp.m), _ptr(self.E), _ptr(self.B),
+                                        _ptr(self.J), int(sp.x.shape[0]), _ptr(sp.x), _ptr(sp.u),
+                                        _ptr(sp.w))
+                if rc != ORC_OK:
+                    raise ValueError(f"oracle push rejected a particle move (code {rc})")
+            L.orc_yee_step(ctypes.byref(self.g), float(self.dt), _ptr(self.E), _ptr(self.B),
+                           _ptr(self.J))
+
+    def rho(self) -> np.ndarray:
+        """Charge density at the nodes, background included."""
+        r = np.full((self.nz, self.ny, self.nx), float(self.rho_bg))
+        for sp in self.species:
+            deposit_rho(self.g, sp.order, sp.q, sp.x, sp.w, r)
+        return r
+
+    def diagnostics(self) -> np.ndarray:
+        """[field energy, kinetic energy, total charge, max |div E - rho|]."""
+        L = lib()
+        wf = L.orc_field_energy(ctypes.byref(self.g), _ptr(self.E), _ptr(self.B))
+        wk = 0.0
+        qtot = float(self.rho_bg) * self.nx * self.ny * self.nz * self.dx[0] * self.dx[1] * self.dx[2]
+        for sp in self.species:
+            wk += L.orc_kinetic_energy(float(sp.m), int(sp.u.shape[0]), _ptr(sp.u), _ptr(sp.w))
+            wsum = float(sp.x.shape[0]) if sp.w is None else float(np.sum(sp.w))
+            qtot += sp.q * wsum
+        gauss = float(np.max(np.abs(div_e(self.g, self.E) - self.rho())))
+        return np.array([wf, wk, qtot, gauss])

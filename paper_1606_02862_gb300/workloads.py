@@ -1,0 +1,228 @@
+"""Seeded synthetic workloads for the explicit PIC step.
+
+This module only draws and lays out initial conditions: particle positions,
+momenta and weights, uniform fields, a Gaussian laser pulse.  It holds none
+of the method's arithmetic (no shape function, gather, push, deposit or field
+update), so both the CUDA path and the FP64 oracle may take their inputs from
+it.  Every array is FP64 and comes from ``numpy.random.default_rng(seed)``
+(PCG64).
+
+Normalised units: c = 1, eps0 = 1, e = m_e = 1, dx = dy = dz = 1, so a
+number density n gives the plasma frequency omega_p = sqrt(n q^2 / m) and the
+critical density of a laser of wavelength lambda cells is
+n_c = (2 pi / lambda)^2.  A macro-particle weight is w = n * V_cell / ppc.
+
+Workloads (sizes as the benchmark table names them):
+  small_cic_32      32^3 periodic, electrons 2 ppc, u_th = 0.01, B_z = 0.1, CIC
+  thermal_tsc_256   256^3 periodic, electrons 8 ppc + neutralising background,
+                    u_th = 0.05, TSC (and its 64^3 sub-run)
+  laser_ramp        128 x 1024 x 128, electrons + protons 4 ppc each in a
+                    linear density ramp, Gaussian laser pulse along y
+  batched_uneven    64 periodic boxes, edges from {16, 24, ..., 96}, ppc from
+                    1..16, u_th from [0.01, 0.1]
+  foil_overdense    256 x 2048 x 256, a 20-cell foil of electrons + C6+ at
+                    30 n_c, 16 ppc each, Gaussian laser a0 = 10
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+BASE_SEED = 160602862  # arXiv 1606.02862
+COURANT_3D = 1.0 / math.sqrt(3.0)  # for dx = dy = dz = 1
+DT_HALF_COURANT = 0.5 * COURANT_3D
+PROTON_MASS = 1836.15267
+C6_MASS = 12.0 * 1822.888486 - 6.0  # carbon-12 nucleus in electron masses
+
+
+@dataclass
+class SpeciesDef:
+    name: str
+    q: float
+    m: float
+    shape: int  # 1 = CIC, 2 = TSC
+    mobile: bool = True
+
+
+@dataclass
+class BoxInit:
+    nx: int
+    ny: int
+    nz: int
+    # per species: (x (n,3), u (n,3), w (n,)) float64
+    particles: list = field(default_factory=list)
+    E: np.ndarray | None = None  # (3, nz, ny, nx) or None = zero
+    B: np.ndarray | None = None
+    rho_bg: float = 0.0
+
+    @property
+    def ncells(self) -> int:
+        return self.nx * self.ny * self.nz
+
+    @property
+    def nparticles(self) -> int:
+        return int(sum(p[0].shape[0] for p in self.particles))
+
+
+@dataclass
+class Workload:
+    name: str
+    dt: float
+    species: list
+    boxes: list
+    dx: tuple = (1.0, 1.0, 1.0)
+    steps: int = 1
+    note: str = ""
+
+    @property
+    def nparticles(self) -> int:
+        return sum(b.nparticles for b in self.boxes)
+
+    @property
+    def ncells(self) -> int:
+        return sum(b.ncells for b in self.boxes)
+
+
+# ----------------------------------------------------------------- loaders
+
+def uniform_in_cells(rng, nx, ny, nz, ppc, y_lo=0, y_hi=None):
+    """ppc positions drawn uniformly inside every cell of the y-slab
+    [y_lo, y_hi); returns (n, 3) float64 in cell units."""
+    y_hi = ny if y_hi is None else y_hi
+    cz, cy, cx = np.meshgrid(np.arange(nz), np.arange(y_lo, y_hi), np.arange(nx), indexing="ij")
+    base = np.stack([cx.ravel(), cy.ravel(), cz.ravel()], axis=1).astype(np.float64)
+    base = np.repeat(base, ppc, axis=0)
+    x = base + rng.random(base.shape)
+    # rng.random is in [0, 1); keep the sum strictly inside the box
+    np.minimum(x, np.array([nx, ny, nz], dtype=np.float64) * (1.0 - 2.0 ** -52), out=x)
+    return x
+
+
+def maxwellian(rng, n, u_th, drift=(0.0, 0.0, 0.0)):
+    """Each momentum component drawn independently from N(drift, u_th^2)."""
+    return rng.normal(0.0, u_th, size=(n, 3)) + np.asarray(drift, dtype=np.float64)
+
+
+def uniform_field(nx, ny, nz, comp, value):
+    f = np.zeros((3, nz, ny, nx))
+    f[comp] = value
+    return f
+
+
+def gaussian_pulse_y(nx, ny, nz, a0, lam, waist, duration, y_c, x_c=None, z_c=None):
+    """Linearly polarised (E along x) Gaussian pulse travelling along +y:
+    Ex = a0 w_L exp(-r^2/waist^2) exp(-(y-y_c)^2/duration^2) cos(k (y-y_c)),
+    Bz = -Ex, each sampled at its own staggered Yee position.  waist and
+    duration are 1/e field radii in cells; w_L = k = 2 pi / lam."""
+    k = 2.0 * math.pi / lam
+    x_c = nx / 2.0 if x_c is None else x_c
+    z_c = nz / 2.0 if z_c is None else z_c
+
+    def profile(xs, ys, zs):
+        r2 = (xs - x_c) ** 2 + (zs - z_c) ** 2
+        return a0 * k * np.exp(-r2 / waist ** 2) * np.exp(-((ys - y_c) ** 2) / duration ** 2) * \
+            np.cos(k * (ys - y_c))
+
+    z, y, x = np.meshgrid(np.arange(nz, dtype=np.float64), np.arange(ny, dtype=np.float64),
+                          np.arange(nx, dtype=np.float64), indexing="ij")
+    E = np.zeros((3, nz, ny, nx))
+    B = np.zeros((3, nz, ny, nx))
+    E[0] = profile(x + 0.5, y, z)          # Ex at (i+1/2, j, k)
+    B[2] = -profile(x + 0.5, y + 0.5, z)   # Bz at (i+1/2, j+1/2, k)
+    return E, B
+
+
+# ----------------------------------------------------------------- configs
+
+def small_cic_32(n=32, ppc=2, seed_offset=0) -> Workload:
+    """32^3 periodic, one electron species 2 ppc, Maxwellian u_th = 0.01,
+    uniform B_z = 0.1, zero E, CIC; electron density 0.01 with a fixed
+    neutralising background so the zero initial E satisfies Gauss's law."""
+    rng = np.random.default_rng(BASE_SEED + seed_offset)
+    dens = 0.01
+    x = uniform_in_cells(rng, n, n, n, ppc)
+    u = maxwellian(rng, x.shape[0], 0.01)
+    w = np.full(x.shape[0], dens / ppc)
+    box = BoxInit(n, n, n, particles=[(x, u, w)], B=uniform_field(n, n, n, 2, 0.1), rho_bg=dens)
+    return Workload("small_cic_32", DT_HALF_COURANT, [SpeciesDef("e", -1.0, 1.0, 1)], [box],
+                    steps=100)
+
+
+def thermal_tsc(n=256, ppc=8, u_th=0.05, seed_offset=1, ny=None, nz=None) -> Workload:
+    """n^3 periodic, electrons ppc per cell, Maxwellian u_th, TSC, density
+    0.01 plus a fixed neutralising background.  n = 64 is the sub-run the
+    FP64 oracle can follow."""
+    ny = n if ny is None else ny
+    nz = n if nz is None else nz
+    rng = np.random.default_rng(BASE_SEED + seed_offset)
+    dens = 0.01
+    x = uniform_in_cells(rng, n, ny, nz, ppc)
+    u = maxwellian(rng, x.shape[0], u_th)
+    w = np.full(x.shape[0], dens / ppc)
+    box = BoxInit(n, ny, nz, particles=[(x, u, w)], rho_bg=dens)
+    return Workload(f"thermal_tsc_{n}", DT_HALF_COURANT, [SpeciesDef("e", -1.0, 1.0, 2)], [box],
+                    steps=200)
+
+
+def laser_ramp(nx=128, ny=1024, nz=128, ppc=4, seed_offset=2, lam=32.0, a0=3.0, waist=16.0,
+               duration=40.0, y_c=80.0, ramp=(160, 360), n_frac=0.01) -> Workload:
+    """Electron + proton species, ppc each, density rising linearly from 0 at
+    y = ramp[0] to n_frac n_c at y = ramp[1], then flat; Gaussian pulse along
+    y.  Weights follow the local density at each particle's cell row."""
+    rng = np.random.default_rng(BASE_SEED + seed_offset)
+    nc = (2.0 * math.pi / lam) ** 2
+    n0 = n_frac * nc
+    y_lo = min(ramp[0], ny)
+    xs = []
+    for _sp in range(2):
+        x = uniform_in_cells(rng, nx, ny, nz, ppc, y_lo=y_lo, y_hi=ny)
+        row = np.floor(x[:, 1]) + 0.5
+        dens = n0 * np.clip((row - ramp[0]) / (ramp[1] - ramp[0]), 0.0, 1.0)
+        xs.append((x, dens / ppc))
+    ue = maxwellian(rng, xs[0][0].shape[0], 0.001)
+    ui = maxwellian(rng, xs[1][0].shape[0], 0.001 / math.sqrt(PROTON_MASS))
+    E, B = gaussian_pulse_y(nx, ny, nz, a0, lam, waist, duration, y_c)
+    box = BoxInit(nx, ny, nz, particles=[(xs[0][0], ue, xs[0][1]), (xs[1][0], ui, xs[1][1])],
+                  E=E, B=B)
+    sp = [SpeciesDef("e", -1.0, 1.0, 2), SpeciesDef("p", 1.0, PROTON_MASS, 2)]
+    return Workload("laser_ramp", DT_HALF_COURANT, sp, [box], steps=1000)
+
+
+def batched_uneven(nboxes=64, seed_offset=3, sizes=tuple(range(16, 97, 8)), max_ppc=16) -> Workload:
+    """nboxes independent periodic cubic boxes; edge drawn uniformly from
+    sizes, ppc from 1..max_ppc, u_th from U[0.01, 0.1]; electrons, TSC,
+    density 0.01 plus background."""
+    rng = np.random.default_rng(BASE_SEED + seed_offset)
+    boxes = []
+    dens = 0.01
+    for _ in range(nboxes):
+        n = int(rng.choice(sizes))
+        ppc = int(rng.integers(1, max_ppc + 1))
+        u_th = float(rng.uniform(0.01, 0.1))
+        x = uniform_in_cells(rng, n, n, n, ppc)
+        u = maxwellian(rng, x.shape[0], u_th)
+        w = np.full(x.shape[0], dens / ppc)
+        boxes.append(BoxInit(n, n, n, particles=[(x, u, w)], rho_bg=dens))
+    return Workload("batched_uneven", DT_HALF_COURANT, [SpeciesDef("e", -1.0, 1.0, 2)], boxes,
+                    steps=500)
+
+
+def foil_overdense(nx=256, ny=2048, nz=256, ppc=16, seed_offset=4, lam=32.0, a0=10.0,
+                   waist=16.0, duration=40.0, foil=(512, 532), n_e_over_nc=30.0) -> Workload:
+    """A foil y in [foil[0], foil[1]) of electrons at n_e_over_nc n_c and C6+
+    at a sixth of that (neutral), ppc each, in vacuum; Gaussian pulse centred
+    100 cells before the foil."""
+    rng = np.random.default_rng(BASE_SEED + seed_offset)
+    nc = (2.0 * math.pi / lam) ** 2
+    ne = n_e_over_nc * nc
+    xe = uniform_in_cells(rng, nx, ny, nz, ppc, y_lo=foil[0], y_hi=foil[1])
+    xi = uniform_in_cells(rng, nx, ny, nz, ppc, y_lo=foil[0], y_hi=foil[1])
+    ue = maxwellian(rng, xe.shape[0], 0.001)
+    ui = maxwellian(rng, xi.shape[0], 0.001 / math.sqrt(C6_MASS))
+    E, B = gaussian_pulse_y(nx, ny, nz, a0, lam, waist, duration, foil[0] - 100.0)
+    box = BoxInit(nx, ny, nz, particles=[(xe, ue, np.full(xe.shape[0], ne / ppc)),
+                                         (xi, ui, np.full(xi.shape[0], ne / 6.0 / ppc))], E=E, B=B)
+    sp = [SpeciesDef("e", -1.0, 1.0, 2), SpeciesDef("C6+", 6.0, C6_MASS, 2)]
+    return Workload("foil_overdense", DT_HALF_COURANT, sp, [box], steps=2000)
