@@ -1,0 +1,412 @@
+"""Benchmark of the explicit PIC step on one GB300 (or N, one process each).
+
+Workload (default): thermal_tsc_256 -- a 256^3 periodic box, one electron
+species at 8 particles per cell (134,217,728 particles), Maxwellian
+u_th = 0.05 c, TSC shape, density 0.01 over a fixed neutralising
+background, dt = 0.5 x the 3D Courant limit; synthetic, seeded.
+
+Metric: particle updates per second in push+deposit (field gather, Boris,
+move, Esirkepov deposition, frame maintenance) of the mixed form
+(int32 cell + FP32 offsets in supercell frames), with the whole step
+captured in a CUDA graph.  Reported alongside: the plain FP64 GPU form on
+the same workload, the full-step rate (adds the Yee update), the HBM
+roofline fraction of the push+deposit kernel, an end-to-end number through
+the C ABI from pinned host buffers, and the FP64 oracle timed on a bounded
+sample on this host's cores.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle updates/sec (push+deposit) at 1 GB300 and % of HBM roofline, batched FP32 vs plain"
+UNIT = "particle updates/s"
+FALLBACK_HBM_GBS = 6800.0
+# algorithmic HBM bytes per unit (mixed form): particle read 32 B + write 28 B
+# (the weight is read-only); fields: E, B read 24 B/cell, J written 12 B/cell
+MIXED_BYTES_PER_PARTICLE = 60.0
+MIXED_BYTES_PER_CELL = 36.0
+# plain FP64 form: particle read 56 B + write 48 B; fields 48 + 24 B/cell
+PLAIN_BYTES_PER_PARTICLE = 104.0
+PLAIN_BYTES_PER_CELL = 72.0
+PUSH_KERNEL_SRC = os.path.join(ROOT, "paper_1606_02862_gb300", "csrc", "k_push.cu")
+TRAFFIC_SUMMARY = os.path.join(ROOT, "profiles", "push_deposit_thermal_tsc.md")
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def measured_hbm():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:  # noqa: BLE001 - absent on a machine without the driver's file
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def push_traffic_per_particle():
+    """DRAM bytes per particle of the push kernel from the committed ncu
+    summary, or None when the summary is absent or the kernel changed since."""
+    try:
+        with open(PUSH_KERNEL_SRC, "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()
+        vals = {}
+        with open(TRAFFIC_SUMMARY) as f:
+            for line in f:
+                if ":" in line and line.strip().startswith("- "):
+                    k, v = line.strip()[2:].split(":", 1)
+                    vals[k.strip()] = v.strip().strip("`")
+        if vals.get("k_push.cu sha256") != sha:
+            return None
+        return float(vals["dram bytes per particle"])
+    except Exception:  # noqa: BLE001
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:  # noqa: BLE001
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:  # noqa: BLE001
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                rows.append((float(parts[0]), float(parts[1]), parts[4:8]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        busy = [r for r in rows if r[0] > 0]
+        sm = sorted(r[0] for r in busy) or [0.0]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[2][i].lower() == "active"})
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ----------------------------------------------------------------------------- ours
+
+def make_state(torch, n, ppc, u_th, pinned=True):
+    from paper_1606_02862_gb300 import workloads as W
+
+    npart = n * n * n * ppc
+    X = torch.empty((npart, 3), dtype=torch.float64, pin_memory=pinned)
+    U = torch.empty((npart, 3), dtype=torch.float64, pin_memory=pinned)
+    Wt = torch.empty((npart,), dtype=torch.float64, pin_memory=pinned)
+    W.fill_thermal(X.numpy(), U.numpy(), Wt.numpy(), n, n, n, ppc, u_th)
+    return X, U, Wt
+
+
+def new_ctx(pic, n, precision, sc, threads):
+    from paper_1606_02862_gb300 import workloads as W
+
+    ctx = pic.Context([(n, n, n)], (1.0, 1.0, 1.0), W.DT_HALF_COURANT,
+                      [pic.Species(-1.0, 1.0, 2, True)], precision=precision, sc=sc,
+                      threads_per_sc=threads, use_graph=True)
+    ctx.set_background(0, 0.01)
+    return ctx
+
+
+def load(ctx, X, U, Wt):
+    n = X.shape[0]
+    ctx.load_particles_ptr(0, 0, n, X.data_ptr(), U.data_ptr(), Wt.data_ptr())
+
+
+def cpu_baseline_oracle(steps=5, n=32, ppc=8):
+    """The FP64 oracle on a bounded sample of the same recipe (n^3 box)."""
+    import oracle
+    from paper_1606_02862_gb300 import workloads as W
+
+    oracle.build()
+    wl = W.thermal_tsc(n=n, ppc=ppc, u_th=0.05)
+    b = wl.boxes[0]
+    x, u, w = b.particles[0]
+    st = oracle.State(n, n, n, wl.dt, species=[oracle.Species(-1.0, 1.0, 2, x, u, w)], rho_bg=b.rho_bg)
+    t0 = time.perf_counter()
+    st.step(steps)
+    dt = time.perf_counter() - t0
+    return {"value": x.shape[0] * steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"thermal_tsc recipe on a {n}^3 box ({x.shape[0]} particles, TSC, 8 ppc), "
+                      f"{steps} full steps, single-threaded FP64 C oracle ({dt:.1f} s)",
+            "cpu": cpu_model()}
+
+
+def cpu_model():
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part", "hardware")):
+                    return line.split(":", 1)[1].strip()
+    except Exception:  # noqa: BLE001
+        pass
+    return os.uname().machine
+
+
+def run_ours(args, rank, world, dist):
+    import torch
+
+    from paper_1606_02862_gb300 import build as libbuild
+    from paper_1606_02862_gb300 import pic
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if rank == 0 or not os.path.exists(pic.LIB_PATH):
+        libbuild.build()
+    if dist is not None:
+        dist.barrier()
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+
+    n, ppc, u_th = args.n, 8, 0.05
+    sc = tuple(int(v) for v in args.sc.split("x"))
+    ncell = n ** 3
+    t0 = time.perf_counter()
+    X, U, Wt = make_state(torch, n, ppc, u_th)
+    npart = X.shape[0]
+    log(f"[rank {rank}] generated {npart} particles in {time.perf_counter() - t0:.1f} s")
+
+    hbm, hbm_src = measured_hbm()
+    result = {}
+
+    # ---------------- mixed form, device-resident inputs, graph replay
+    ctx = new_ctx(pic, n, pic.PRECISION_MIXED, sc, args.threads)
+    t0 = time.perf_counter()
+    load(ctx, X, U, Wt)
+    log(f"[rank {rank}] loaded in {time.perf_counter() - t0:.1f} s")
+    ctx.step(args.warmup)
+    ctx.stage_timing(True)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        ctx.step_async(args.steps)
+        ev1.record(stream)
+        ctx.sync()
+        torch.cuda.synchronize()
+    total_ms = ev0.elapsed_time(ev1)
+    stage_ms, nst = ctx.stage_times()
+    graph = bool(ctx.info(pic.INFO_GRAPH_ACTIVE))
+    kernels = ctx.info(pic.INFO_KERNELS_PER_STEP)
+    assert nst == args.steps, (nst, args.steps)
+    ctx.stage_timing(False)
+    ctx.close()
+    push_ms = stage_ms[0] / args.steps
+    frames_ms = stage_ms[1] / args.steps
+    yee_ms = stage_ms[2] / args.steps
+    step_ms = total_ms / args.steps
+    pd_ms = push_ms + frames_ms
+    times = torch.tensor([pd_ms, step_ms], dtype=torch.float64)
+    if dist is not None:
+        t = times.cuda()
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        times = t.cpu()
+    pd_ms_max, step_ms_max = float(times[0]), float(times[1])
+    value = world * npart / (pd_ms_max * 1e-3)
+    push_bytes = npart * MIXED_BYTES_PER_PARTICLE + ncell * MIXED_BYTES_PER_CELL
+    achieved = push_bytes / (push_ms * 1e-3) / 1e9
+    tpp = push_traffic_per_particle()
+    result.update(value=value, step_ms=step_ms_max, push_ms=push_ms, frames_ms=frames_ms,
+                  yee_ms=yee_ms, graph=graph, kernels=kernels, achieved=achieved,
+                  traffic=None if tpp is None else tpp * npart, clocks=clk.summary())
+    log(f"[rank {rank}] mixed: push {push_ms:.3f} ms, frames {frames_ms:.3f} ms, yee {yee_ms:.3f} ms,"
+        f" step {step_ms:.3f} ms, graph={graph}")
+
+    # ---------------- end to end through the C ABI from pinned host buffers
+    if not args.no_e2e:
+        Xo = torch.empty_like(X, pin_memory=True)
+        Uo = torch.empty_like(U, pin_memory=True)
+        Wo = torch.empty_like(Wt, pin_memory=True)
+        Eo = np.empty((3, n, n, n))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx = new_ctx(pic, n, pic.PRECISION_MIXED, sc, args.threads)
+        load(ctx, X, U, Wt)
+        ctx.step(args.steps)
+        nout = ctx.read_particles_ptr(0, 0, npart, Xo.data_ptr(), Uo.data_ptr(), Wo.data_ptr())
+        ctx.read_fields_ptr(0, pic.FIELD_E, Eo.ctypes.data)
+        t_e2e = time.perf_counter() - t0
+        ctx.close()
+        h2d = npart * 56.0
+        d2h = nout * 56.0 + Eo.nbytes
+        result["e2e"] = {"value": world * npart * args.steps / t_e2e, "unit": UNIT,
+                         "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+                         "seconds": t_e2e,
+                         "what": "pic_create + pic_load_particles (pinned FP64 host) + K x pic_step "
+                                 "+ pic_read_particles + pic_read_fields(E), wall clock"}
+        log(f"[rank {rank}] e2e {t_e2e:.2f} s")
+        del Xo, Uo, Wo
+
+    # ---------------- plain FP64 GPU form, same workload
+    if not args.no_plain:
+        ctx = new_ctx(pic, n, pic.PRECISION_FP64_PLAIN, sc, 0)
+        load(ctx, X, U, Wt)
+        ctx.step(1)
+        ctx.stage_timing(True)
+        ctx.step(args.plain_steps)
+        ms, nst = ctx.stage_times()
+        ctx.close()
+        p_ms = ms[0] / nst
+        p_bytes = npart * PLAIN_BYTES_PER_PARTICLE + ncell * PLAIN_BYTES_PER_CELL
+        result["plain"] = {"value": world * npart / (p_ms * 1e-3), "unit": UNIT,
+                           "push_ms": p_ms, "step_ms": ms[3] / nst, "steps": nst,
+                           "hbm_frac": p_bytes / (p_ms * 1e-3) / 1e9 / hbm,
+                           "bytes_per_particle": PLAIN_BYTES_PER_PARTICLE}
+        log(f"[rank {rank}] plain fp64: push {p_ms:.2f} ms")
+
+    if rank != 0:
+        return None
+    line = {
+        "metric": METRIC, "value": result["value"], "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": result["step_ms"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": f"thermal_tsc_{n}: {n}^3 periodic cells, electrons {ppc} ppc "
+                               f"({npart} particles/GPU), u_th 0.05c, TSC, dt = 0.5 Courant, "
+                               "neutralising background",
+                   "form": f"mixed: int32 cell + FP32 offsets, supercell frames {args.sc}, "
+                           f"{args.threads or 'default'} threads/supercell",
+                   "graph": result["graph"],
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "l2": "inputs larger than L2 (particles 4.3 GB/GPU)"},
+        "push_deposit_ms_per_step": result["push_ms"] + result["frames_ms"],
+        "stage_ms_per_step": {"push_deposit_kernel": result["push_ms"],
+                              "frame_maintenance": result["frames_ms"], "yee": result["yee_ms"]},
+        "full_step_rate": world * npart / (result["step_ms"] * 1e-3),
+        "roofline": {"bound": "hbm", "achieved": result["achieved"], "peak": hbm, "unit": "GB/s",
+                     "frac": result["achieved"] / hbm, "traffic": result["traffic"],
+                     "kernel": "k_push_deposit", "peak_source": hbm_src,
+                     "bytes_per_launch": npart * MIXED_BYTES_PER_PARTICLE + ncell * MIXED_BYTES_PER_CELL},
+        "gpu_launches": int(result["kernels"] * args.steps),
+        "clocks": result["clocks"],
+    }
+    if "plain" in result:
+        line["plain_fp64"] = result["plain"]
+    if "e2e" in result:
+        line["e2e"] = result["e2e"]
+    if world == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline_oracle()
+    return line
+
+
+# ----------------------------------------------------------------------------- reference arm
+
+def run_reference(args, rank):
+    """The FP64 oracle as it stands, on this host's cores: each step is one
+    full PIC step of a bounded sample (16^3 box, same recipe)."""
+    if rank != 0:
+        return None
+    import oracle
+    from paper_1606_02862_gb300 import workloads as W
+
+    oracle.build()
+    n = 16
+    wl = W.thermal_tsc(n=n, ppc=8, u_th=0.05)
+    b = wl.boxes[0]
+    x, u, w = b.particles[0]
+    st = oracle.State(n, n, n, wl.dt, species=[oracle.Species(-1.0, 1.0, 2, x, u, w)], rho_bg=b.rho_bg)
+    st.step(args.warmup)
+    t0 = time.perf_counter()
+    st.step(args.steps)
+    dt = time.perf_counter() - t0
+    v = x.shape[0] * args.steps / dt
+    sample = (f"thermal_tsc recipe on a {n}^3 box ({x.shape[0]} particles, TSC, 8 ppc) per step, "
+              "single-threaded FP64 C oracle")
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"thermal_tsc_{args.n} (sampled: {n}^3 box per step)"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=256, help="box edge in cells")
+    ap.add_argument("--sc", default="4x4x4", help="supercell edges, e.g. 8x8x4")
+    ap.add_argument("--threads", type=int, default=0)
+    ap.add_argument("--plain-steps", type=int, default=3)
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_mod
+
+        dist_mod.init_process_group("nccl" if args.impl == "ours" else "gloo")
+        dist = dist_mod
+    if args.impl == "reference":
+        line = run_reference(args, rank)
+    else:
+        line = run_ours(args, rank, world, dist)
+    if rank == 0 and line is not None:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

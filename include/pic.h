@@ -23,8 +23,8 @@
  * B^{n+1} = B^{n+1/2} - dt/2 curl E^{n+1}.
  *
  * Threading: a context is used from one host thread at a time.  All device
- * work of a context runs on the stream given in pic_options (or the legacy
- * default stream when it is NULL).
+ * work of a context runs on the stream given in pic_options (or on a stream
+ * of its own when that is NULL).
  *
  * Errors: every call returns a pic_status and never aborts, throws or exits.
  * After any error other than PIC_ERR_ARG the context is poisoned: every later
@@ -96,7 +96,8 @@ typedef struct {
     void* (*dev_alloc)(size_t bytes, void* alloc_ud);
     void (*dev_free)(void* ptr, void* alloc_ud);
     void* alloc_ud;
-    void* stream;           /* cudaStream_t for all device work; NULL = legacy default stream */
+    void* stream;           /* cudaStream_t for all device work; NULL = a non-blocking stream the
+                               context creates (graph capture needs a non-default stream) */
 } pic_options;
 
 /*
@@ -204,6 +205,24 @@ pic_status pic_diagnostics(pic_ctx* ctx, int32_t box, double out[4]);
  */
 pic_status pic_stage_timing(pic_ctx* ctx, int32_t enable);
 pic_status pic_stage_times(pic_ctx* ctx, double ms[4], int64_t* nsteps_out);
+
+/*
+ * pic_info -- one integer property of the context into *out:
+ *   PIC_INFO_GRAPH_ACTIVE    1 if pic_step replays captured CUDA graphs (mixed form,
+ *                            after the first step), else 0;
+ *   PIC_INFO_KERNELS_PER_STEP number of libpic kernel launches one step makes;
+ *   PIC_INFO_POOL_FRAMES     frame-pool capacity (mixed form);
+ *   PIC_INFO_FRAMES_USED     frames holding particles, read from the device;
+ *   PIC_INFO_MOVE_CAPACITY   capacity of the per-step buffer of particles changing supercell.
+ */
+enum {
+    PIC_INFO_GRAPH_ACTIVE = 0,
+    PIC_INFO_KERNELS_PER_STEP = 1,
+    PIC_INFO_POOL_FRAMES = 2,
+    PIC_INFO_FRAMES_USED = 3,
+    PIC_INFO_MOVE_CAPACITY = 4
+};
+pic_status pic_info(pic_ctx* ctx, int32_t key, int64_t* out);
 
 /* pic_last_error -- human-readable message of the last error (never NULL). */
 const char* pic_last_error(const pic_ctx* ctx);

@@ -1,0 +1,353 @@
+// k_fields.cu -- Yee FDTD update (Yee 1966, the "Yee field solver" of Sec. 4)
+// for the mixed form's guard-padded FP32 fields, field import/export, and
+// the FP64 diagnostics reductions.
+//
+// Staggering: Ex(i+1/2,j,k) Ey(i,j+1/2,k) Ez(i,j,k+1/2), Bx(i,j+1/2,k+1/2)
+// By(i+1/2,j,k+1/2) Bz(i+1/2,j+1/2,k); J with E.  One step of the field
+// half of the cycle:
+//   B^{n+1/2} = B^n - dt/2 curl E^n
+//   E^{n+1}   = E^n + dt (curl B^{n+1/2} - J^{n+1/2})
+//   B^{n+1}   = B^{n+1/2} - dt/2 curl E^{n+1}
+// Every kernel writes each updated interior value also into its periodic
+// guard images, so the next kernel (and the next push's tile loads) read
+// guards without a separate exchange.  The E kernel first folds the J guard
+// images (deposits that spilled over the periodic seam) into the interior,
+// leaves the folded J in the interior and zeroes the guards.
+//
+// One launch covers all boxes: blocks of 32 x 8 cells in x-y, one z layer,
+// box found from a per-box block offset table.
+#include "pic_internal.cuh"
+
+#include <cmath>
+
+namespace pic {
+
+struct YeeArgs {
+    const BoxDev* boxes;
+    const int* blk_off;  // [nboxes + 1]
+    int nboxes;
+    float tau;           // dt/2 for the B halves, dt for E
+    float ih[3];         // 1 / h_d
+};
+
+__device__ __forceinline__ int find_box(const int* off, int n, int blk)
+{
+    int lo = 0, hi = n;  // off[lo] <= blk < off[hi]
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (off[mid] <= blk)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+struct CellAt {
+    int x, y, z;
+    bool ok;
+};
+
+__device__ __forceinline__ CellAt yee_cell(const YeeArgs& a, BoxDev& b)
+{
+    const int box = find_box(a.blk_off, a.nboxes, blockIdx.x);
+    b = a.boxes[box];
+    const int local = blockIdx.x - a.blk_off[box];
+    const int nbx = (b.nx + 31) >> 5, nby = (b.ny + 7) >> 3;
+    CellAt c;
+    c.x = (local % nbx) * 32 + threadIdx.x;
+    c.y = ((local / nbx) % nby) * 8 + threadIdx.y;
+    c.z = local / (nbx * nby);
+    c.ok = c.x < b.nx && c.y < b.ny;
+    return c;
+}
+
+// Periodic images of an interior coordinate inside the padded range
+// (x: -1 .. n+2, y and z: -1 .. n+1).  Returns the count (1..2), [0] = itself.
+__device__ __forceinline__ int images(int v, int n, int hi_guard, int* out)
+{
+    out[0] = v;
+    if (v < hi_guard) {
+        out[1] = v + n;
+        return 2;
+    }
+    if (v == n - 1) {
+        out[1] = -1;
+        return 2;
+    }
+    return 1;
+}
+
+__device__ __forceinline__ void store_with_images(const BoxDev& b, float* F, const CellAt& c,
+                                                  float v)
+{
+    int ix[2], iy[2], iz[2];
+    int nx = images(c.x, b.nx, 3, ix), ny = images(c.y, b.ny, 2, iy), nz = images(c.z, b.nz, 2, iz);
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i)
+                F[padded_index(b, ix[i], iy[j], iz[k])] = v;
+}
+
+__global__ void __launch_bounds__(256) k_yee_b(const YeeArgs a)
+{
+    BoxDev b;
+    CellAt c = yee_cell(a, b);
+    if (!c.ok)
+        return;
+    const int64_t pc = padded_cells(b);
+    const int64_t sx = 1, sy = b.px, sz = (int64_t)b.px * b.py;
+    const int64_t i = padded_index(b, c.x, c.y, c.z);
+    const float *Ex = b.E, *Ey = b.E + pc, *Ez = b.E + 2 * pc;
+    float *Bx = b.B, *By = b.B + pc, *Bz = b.B + 2 * pc;
+    const float ex = Ex[i], ey = Ey[i], ez = Ez[i];
+    const float cx = (Ez[i + sy] - ez) * a.ih[1] - (Ey[i + sz] - ey) * a.ih[2];
+    const float cy = (Ex[i + sz] - ex) * a.ih[2] - (Ez[i + sx] - ez) * a.ih[0];
+    const float cz = (Ey[i + sx] - ey) * a.ih[0] - (Ex[i + sy] - ex) * a.ih[1];
+    store_with_images(b, Bx, c, Bx[i] - a.tau * cx);
+    store_with_images(b, By, c, By[i] - a.tau * cy);
+    store_with_images(b, Bz, c, Bz[i] - a.tau * cz);
+}
+
+__global__ void __launch_bounds__(256) k_yee_e(const YeeArgs a)
+{
+    BoxDev b;
+    CellAt c = yee_cell(a, b);
+    if (!c.ok)
+        return;
+    const int64_t pc = padded_cells(b);
+    const int64_t sx = 1, sy = b.px, sz = (int64_t)b.px * b.py;
+    const int64_t i = padded_index(b, c.x, c.y, c.z);
+    // fold the J guard images into the interior
+    int ix[2], iy[2], iz[2];
+    int nx = images(c.x, b.nx, 3, ix), ny = images(c.y, b.ny, 2, iy), nz = images(c.z, b.nz, 2, iz);
+    float jx = 0.f, jy = 0.f, jz = 0.f;
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int q = 0; q < nx; ++q) {
+                int64_t g = padded_index(b, ix[q], iy[j], iz[k]);
+                jx += b.J[g];
+                jy += b.J[pc + g];
+                jz += b.J[2 * pc + g];
+                if (g != i) {
+                    b.J[g] = 0.f;
+                    b.J[pc + g] = 0.f;
+                    b.J[2 * pc + g] = 0.f;
+                }
+            }
+    b.J[i] = jx;
+    b.J[pc + i] = jy;
+    b.J[2 * pc + i] = jz;
+    const float *Bx = b.B, *By = b.B + pc, *Bz = b.B + 2 * pc;
+    float *Ex = b.E, *Ey = b.E + pc, *Ez = b.E + 2 * pc;
+    const float bx = Bx[i], by = By[i], bz = Bz[i];
+    const float cx = (bz - Bz[i - sy]) * a.ih[1] - (by - By[i - sz]) * a.ih[2];
+    const float cy = (bx - Bx[i - sz]) * a.ih[2] - (bz - Bz[i - sx]) * a.ih[0];
+    const float cz = (by - By[i - sx]) * a.ih[0] - (bx - Bx[i - sy]) * a.ih[1];
+    store_with_images(b, Ex, c, Ex[i] + a.tau * (cx - jx));
+    store_with_images(b, Ey, c, Ey[i] + a.tau * (cy - jy));
+    store_with_images(b, Ez, c, Ez[i] + a.tau * (cz - jz));
+}
+
+cudaError_t launch_yee_mixed_plan(const YeePlan& p, cudaStream_t st)
+{
+    YeeArgs a{p.boxes, p.blk_off, p.nboxes, 0.5f * p.dt, {p.ih[0], p.ih[1], p.ih[2]}};
+    dim3 blk(32, 8);
+    k_yee_b<<<p.nblocks, blk, 0, st>>>(a);
+    a.tau = p.dt;
+    k_yee_e<<<p.nblocks, blk, 0, st>>>(a);
+    a.tau = 0.5f * p.dt;
+    k_yee_b<<<p.nblocks, blk, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ import/export
+
+// src: FP64 [3][nz][ny][nx] on the device -> padded FP32 field with images.
+__global__ void k_fields_to_padded(const BoxDev b, float* F, const double* src)
+{
+    const int64_t n = (int64_t)b.nx * b.ny * b.nz;
+    const int64_t pc = padded_cells(b);
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < 3 * n;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        int comp = (int)(t / n);
+        int64_t r = t - comp * n;
+        CellAt c;
+        c.x = (int)(r % b.nx);
+        c.y = (int)((r / b.nx) % b.ny);
+        c.z = (int)(r / ((int64_t)b.nx * b.ny));
+        store_with_images(b, F + comp * pc, c, (float)src[t]);
+    }
+}
+
+__global__ void k_fields_from_padded(const BoxDev b, const float* F, double* dst)
+{
+    const int64_t n = (int64_t)b.nx * b.ny * b.nz;
+    const int64_t pc = padded_cells(b);
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < 3 * n;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        int comp = (int)(t / n);
+        int64_t r = t - comp * n;
+        int x = (int)(r % b.nx), y = (int)((r / b.nx) % b.ny), z = (int)(r / ((int64_t)b.nx * b.ny));
+        dst[t] = (double)F[comp * pc + padded_index(b, x, y, z)];
+    }
+}
+
+cudaError_t launch_fields_to_padded(const BoxDev& b, int which, const double* src, cudaStream_t st)
+{
+    float* F = which == 0 ? b.E : (which == 1 ? b.B : b.J);
+    k_fields_to_padded<<<1024, 256, 0, st>>>(b, F, src);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fields_from_padded(const BoxDev& b, int which, double* dst, cudaStream_t st)
+{
+    const float* F = which == 0 ? b.E : (which == 1 ? b.B : b.J);
+    k_fields_from_padded<<<1024, 256, 0, st>>>(b, F, dst);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ FP64 diagnostics
+
+__device__ __forceinline__ double block_sum(double v)
+{
+    __shared__ double s[32];
+    for (int o = 16; o > 0; o >>= 1)
+        v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0)
+        s[wid] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < (int)(blockDim.x + 31) / 32; ++i)
+            r += s[i];
+    __syncthreads();
+    return r;
+}
+
+__global__ void k_diag_fields(const BoxDev b, double* out, double vol)
+{
+    const int64_t n = (int64_t)b.nx * b.ny * b.nz;
+    const int64_t pc = padded_cells(b);
+    double acc = 0.0;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        int x = (int)(t % b.nx), y = (int)((t / b.nx) % b.ny), z = (int)(t / ((int64_t)b.nx * b.ny));
+        int64_t i = padded_index(b, x, y, z);
+        for (int c = 0; c < 3; ++c) {
+            double e = b.E[c * pc + i], m = b.B[c * pc + i];
+            acc += e * e + m * m;
+        }
+    }
+    double s = block_sum(acc);
+    if (threadIdx.x == 0)
+        atomicAdd(out, 0.5 * s * vol);
+}
+
+// Shape weights in FP64 for the charge density (same shapes as the push).
+__device__ __forceinline__ double shape64(int shape, double d)
+{
+    double a = fabs(d);
+    if (shape == 1)
+        return a < 1.0 ? 1.0 - a : 0.0;
+    if (a <= 0.5)
+        return 0.75 - a * a;
+    return a < 1.5 ? 0.5 * (1.5 - a) * (1.5 - a) : 0.0;
+}
+
+// One CTA per supercell of the box: kinetic energy, charge, and the charge
+// density deposited (FP64 atomics) into rho[nz][ny][nx].
+__global__ void k_diag_particles(const StepDev d, int box, double* rho, double* out, double ivol)
+{
+    const BoxDev b = d.boxes[box];
+    const int loc = blockIdx.x;
+    const int g = b.sc_base + loc;
+    const int scx = loc % b.nscx, scy = (loc / b.nscx) % b.nscy, scz = loc / (b.nscx * b.nscy);
+    double ekin = 0.0, q = 0.0;
+    for (int s = 0; s < d.nspecies; ++s) {
+        const SpeciesDev sp = d.sp[s];
+        const int L = s * d.nsc + g;
+        const int n = d.count[L];
+        const int* ft = d.ftab + d.foff[L];
+        const double mass = (double)sp.m;
+        for (int p = threadIdx.x; p < n; p += blockDim.x) {
+            const int64_t idx = (int64_t)ft[p >> d.log2S] * d.S + (p & (d.S - 1));
+            const double ux = d.ux[idx], uy = d.uy[idx], uz = d.uz[idx], w = d.w[idx];
+            const double u2 = ux * ux + uy * uy + uz * uz;
+            ekin += w * mass * (u2 / (sqrt(1.0 + u2) + 1.0));
+            q += (double)sp.q * w;
+            const int cell = d.cell[idx];
+            const double pos[3] = {(double)(scx * d.LX + cell % d.LX) + (double)d.ox[idx],
+                                   (double)(scy * d.LY + (cell / d.LX) % d.LY) + (double)d.oy[idx],
+                                   (double)(scz * d.LZ + cell / (d.LX * d.LY)) + (double)d.oz[idx]};
+            int base[3];
+            double wt[3][4];
+            const int Nd[3] = {b.nx, b.ny, b.nz};
+            for (int a = 0; a < 3; ++a) {
+                base[a] = (int)floor(pos[a]) - 1;
+                for (int k = 0; k < 4; ++k)
+                    wt[a][k] = shape64(sp.shape, pos[a] - (double)(base[a] + k));
+            }
+            const double qw = (double)sp.q * w * ivol;
+            for (int kz = 0; kz < 4; ++kz)
+                for (int ky = 0; ky < 4; ++ky)
+                    for (int kx = 0; kx < 4; ++kx) {
+                        double v = wt[0][kx] * wt[1][ky] * wt[2][kz];
+                        if (v == 0.0)
+                            continue;
+                        int X = (base[0] + kx + Nd[0]) % Nd[0];
+                        int Y = (base[1] + ky + Nd[1]) % Nd[1];
+                        int Z = (base[2] + kz + Nd[2]) % Nd[2];
+                        atomicAdd(rho + ((int64_t)Z * b.ny + Y) * b.nx + X, qw * v);
+                    }
+        }
+    }
+    double se = block_sum(ekin);
+    double sq = block_sum(q);
+    if (threadIdx.x == 0) {
+        atomicAdd(out + 1, se);
+        atomicAdd(out + 2, sq);
+    }
+}
+
+__global__ void k_diag_gauss(const BoxDev b, const double* rho, double rho_bg, double ih0, double ih1,
+                             double ih2, unsigned long long* maxbits)
+{
+    const int64_t n = (int64_t)b.nx * b.ny * b.nz;
+    const int64_t pc = padded_cells(b);
+    double m = 0.0;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        int x = (int)(t % b.nx), y = (int)((t / b.nx) % b.ny), z = (int)(t / ((int64_t)b.nx * b.ny));
+        int64_t i = padded_index(b, x, y, z);
+        double div = ((double)b.E[i] - (double)b.E[i - 1]) * ih0 +
+                     ((double)b.E[pc + i] - (double)b.E[pc + i - b.px]) * ih1 +
+                     ((double)b.E[2 * pc + i] - (double)b.E[2 * pc + i - (int64_t)b.px * b.py]) * ih2;
+        m = fmax(m, fabs(div - rho[t] - rho_bg));
+    }
+    for (int o = 16; o > 0; o >>= 1)
+        m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0)
+        atomicMax(maxbits, (unsigned long long)__double_as_longlong(m));
+}
+
+cudaError_t launch_diag_mixed(const StepDev& d, const BoxDev& hb, int box, double rho_bg,
+                              double* rho_scratch, double* out, const double h[3], cudaStream_t st)
+{
+    const int64_t n = (int64_t)hb.nx * hb.ny * hb.nz;
+    cudaError_t e = cudaMemsetAsync(rho_scratch, 0, sizeof(double) * n, st);
+    if (e != cudaSuccess)
+        return e;
+    e = cudaMemsetAsync(out, 0, sizeof(double) * 4, st);
+    if (e != cudaSuccess)
+        return e;
+    const double vol = h[0] * h[1] * h[2];
+    k_diag_fields<<<512, 256, 0, st>>>(hb, out, vol);
+    k_diag_particles<<<hb.nscx * hb.nscy * hb.nscz, 128, 0, st>>>(d, box, rho_scratch, out, 1.0 / vol);
+    k_diag_gauss<<<512, 256, 0, st>>>(hb, rho_scratch, rho_bg, 1.0 / h[0], 1.0 / h[1], 1.0 / h[2],
+                                      reinterpret_cast<unsigned long long*>(out + 3));
+    return cudaGetLastError();
+}
+
+}  // namespace pic

@@ -1,0 +1,1275 @@
+// pic_api.cu -- host implementation of the libpic C ABI (include/pic.h).
+//
+// Owns the context: device buffers (through the caller's allocator callback
+// or cudaMalloc), the box and species tables, the frame pool of the mixed
+// form, the per-step CUDA graphs, stage timing, and the device status word.
+// Every entry point returns a pic_status; no exception crosses the ABI.
+#include "pic.h"
+#include "pic_internal.cuh"
+#include "plain.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+using namespace pic;
+
+namespace {
+
+struct PlainSpecies {
+    double *x = nullptr, *y = nullptr, *z = nullptr, *ux = nullptr, *uy = nullptr, *uz = nullptr,
+           *w = nullptr;
+    int* pid = nullptr;
+    int64_t n = 0, cap = 0;
+};
+
+struct PlainBox {
+    double *E = nullptr, *B = nullptr, *J = nullptr;
+    std::vector<PlainSpecies> sp;
+};
+
+constexpr int kStageTimers = 4;  // push, frames, yee, whole step
+
+}  // namespace
+
+struct pic_ctx {
+    // configuration
+    int precision = PIC_PRECISION_MIXED;
+    std::vector<pic_grid> grids;
+    int nboxes = 0;
+    double h[3] = {1, 1, 1};
+    double dt = 0;
+    std::vector<pic_species> sp;
+    pic_options opt{};
+    std::vector<double> rho_bg;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int device = 0;
+    int nsm = 0;
+    size_t smem_optin = 0;
+    // errors
+    std::string err;
+    pic_status poisoned = PIC_OK;
+    // allocations
+    std::vector<void*> allocs;
+    unsigned* status_d = nullptr;
+    double* diag_d = nullptr;
+    double* rho_d = nullptr;
+    int* ioff_d = nullptr;  // scratch ints for read-back offsets
+    int64_t ioff_cap = 0;
+    void* stage_d = nullptr;
+    size_t stage_bytes = 0;
+    // mixed form
+    int LX = 4, LY = 4, LZ = 4, S = 64, log2S = 6, threads = 64;
+    int push_grid = 0;
+    std::vector<BoxDev> boxes_h;
+    BoxDev* boxes_d = nullptr;
+    int* sc_box_d = nullptr;
+    int* items_d = nullptr;
+    int* yee_off_d = nullptr;
+    int yee_nblocks = 0;
+    float *E_all = nullptr, *B_all = nullptr, *J_all = nullptr;
+    int64_t field_floats = 0;  // per field, all boxes (3 components each)
+    int nsc = 0, nlists = 0;
+    int *count = nullptr, *nframes = nullptr, *narrive = nullptr, *abase = nullptr;
+    int* foff[2] = {nullptr, nullptr};
+    int* ftab[2] = {nullptr, nullptr};
+    int *cell = nullptr, *pid = nullptr;
+    float *ox = nullptr, *oy = nullptr, *oz = nullptr, *ux = nullptr, *uy = nullptr, *uz = nullptr,
+          *w = nullptr;
+    int *free_stack = nullptr, *free_top = nullptr, *released = nullptr;
+    int64_t pool_cap = 0;  // frames
+    int64_t frames_used = 0;
+    int mv_cap = 0;
+    int *mv_count = nullptr, *mv_dest = nullptr, *mv_rank = nullptr, *mv_cell = nullptr,
+        *mv_pid = nullptr;
+    float *mv_ox = nullptr, *mv_oy = nullptr, *mv_oz = nullptr, *mv_ux = nullptr, *mv_uy = nullptr,
+          *mv_uz = nullptr, *mv_w = nullptr;
+    int4 *blk_sums = nullptr, *blk_offs = nullptr, *totals = nullptr;
+    int* work_counter = nullptr;
+    unsigned* wmax_bits = nullptr;     // [kMaxSpecies] device
+    float wmax[kMaxSpecies] = {};      // host copy: largest |weight| per species
+    int parity = 0;
+    bool prepared = false;
+    std::vector<int64_t> id_next;  // per (box, species)
+    int64_t total_particles = 0;
+    // graphs (one per frame-table parity); each holds four event-record
+    // nodes at the stage boundaries, re-pointed at fresh events per replay
+    // when stage timing is on
+    cudaGraph_t graph[2] = {nullptr, nullptr};
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    cudaGraphNode_t evnode[2][4] = {};
+    cudaEvent_t placeholder[4] = {};
+    bool graph_failed = false;
+    // plain form
+    std::vector<PlainBox> pboxes;
+    // stage timing
+    bool timing = false;
+    std::vector<cudaEvent_t> events;  // kStageTimers+? per recorded step: 4 boundaries
+    int64_t ev_steps = 0;             // steps with events pending
+    double acc_ms[kStageTimers] = {0, 0, 0, 0};
+    int64_t timed_steps = 0;
+};
+
+namespace {
+
+pic_status fail(pic_ctx* c, pic_status st, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (c) {
+        c->err = buf;
+        if (st != PIC_ERR_ARG && c->poisoned == PIC_OK)
+            c->poisoned = st;
+    }
+    return st;
+}
+
+#define CK(call)                                                                          \
+    do {                                                                                  \
+        cudaError_t e__ = (call);                                                         \
+        if (e__ != cudaSuccess)                                                           \
+            return fail(c, PIC_ERR_CUDA, "%s failed: %s (%s:%d)", #call,                 \
+                        cudaGetErrorString(e__), __FILE__, __LINE__);                     \
+    } while (0)
+
+#define CKS(expr)                     \
+    do {                              \
+        pic_status s__ = (expr);      \
+        if (s__ != PIC_OK)            \
+            return s__;               \
+    } while (0)
+
+void* raw_alloc(pic_ctx* c, size_t bytes)
+{
+    if (bytes == 0)
+        bytes = 256;
+    bytes = (bytes + 255) & ~size_t(255);
+    void* p = nullptr;
+    if (c->opt.dev_alloc) {
+        p = c->opt.dev_alloc(bytes, c->opt.alloc_ud);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    if (p)
+        c->allocs.push_back(p);
+    return p;
+}
+
+void raw_free(pic_ctx* c, void* p)
+{
+    if (!p)
+        return;
+    auto it = std::find(c->allocs.begin(), c->allocs.end(), p);
+    if (it != c->allocs.end())
+        c->allocs.erase(it);
+    if (c->opt.dev_free)
+        c->opt.dev_free(p, c->opt.alloc_ud);
+    else if (!c->opt.dev_alloc)
+        cudaFree(p);
+}
+
+template <class T>
+pic_status dalloc(pic_ctx* c, T** out, int64_t count, bool zero = true)
+{
+    void* p = raw_alloc(c, sizeof(T) * (size_t)std::max<int64_t>(count, 1));
+    if (!p)
+        return fail(c, PIC_ERR_OOM, "device allocation of %lld bytes failed",
+                    (long long)(sizeof(T) * count));
+    if (zero) {
+        cudaError_t e = cudaMemsetAsync(p, 0, sizeof(T) * (size_t)std::max<int64_t>(count, 1),
+                                        c->stream);
+        if (e != cudaSuccess)
+            return fail(c, PIC_ERR_CUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
+    }
+    *out = static_cast<T*>(p);
+    return PIC_OK;
+}
+
+pic_status check_ctx(pic_ctx* c)
+{
+    if (!c)
+        return PIC_ERR_ARG;
+    if (c->poisoned != PIC_OK)
+        return PIC_ERR_STATE;
+    return PIC_OK;
+}
+
+void destroy_graphs(pic_ctx* c)
+{
+    for (int p = 0; p < 2; ++p) {
+        if (c->gexec[p])
+            cudaGraphExecDestroy(c->gexec[p]);
+        if (c->graph[p])
+            cudaGraphDestroy(c->graph[p]);
+        c->gexec[p] = nullptr;
+        c->graph[p] = nullptr;
+    }
+}
+
+pic_status ensure_stage(pic_ctx* c, size_t bytes)
+{
+    if (bytes <= c->stage_bytes)
+        return PIC_OK;
+    CK(cudaStreamSynchronize(c->stream));
+    raw_free(c, c->stage_d);
+    c->stage_d = nullptr;
+    c->stage_bytes = 0;
+    void* p = raw_alloc(c, bytes);
+    if (!p)
+        return fail(c, PIC_ERR_OOM, "staging allocation of %zu bytes failed", bytes);
+    c->stage_d = p;
+    c->stage_bytes = bytes;
+    return PIC_OK;
+}
+
+pic_status ensure_ioff(pic_ctx* c, int64_t n)
+{
+    if (n <= c->ioff_cap)
+        return PIC_OK;
+    CK(cudaStreamSynchronize(c->stream));
+    raw_free(c, c->ioff_d);
+    c->ioff_d = nullptr;
+    CKS(dalloc(c, &c->ioff_d, n, false));
+    c->ioff_cap = n;
+    return PIC_OK;
+}
+
+pic_status status_check(pic_ctx* c)
+{
+    CK(cudaStreamSynchronize(c->stream));
+    unsigned st = 0;
+    CK(cudaMemcpy(&st, c->status_d, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    if (st == 0)
+        return PIC_OK;
+    if (st & ST_FRAME_POOL)
+        return fail(c, PIC_ERR_FRAME_POOL,
+                    "frame pool exhausted (%lld frames); create the context with a larger "
+                    "pool_frames",
+                    (long long)c->pool_cap);
+    if (st & ST_CAPACITY)
+        return fail(c, PIC_ERR_CAPACITY,
+                    "more than %d particles changed supercell in one step; raise move_capacity",
+                    c->mv_cap);
+    if (st & ST_TIMEOUT)
+        return fail(c, PIC_ERR_TIMEOUT, "a device-side wait timed out");
+    return fail(c, PIC_ERR_PARTICLE, "a particle got a non-finite or superluminal momentum");
+}
+
+// ------------------------------------------------------------ mixed form
+
+StepDev make_step(const pic_ctx* c, int parity)
+{
+    StepDev d{};
+    d.LX = c->LX;
+    d.LY = c->LY;
+    d.LZ = c->LZ;
+    d.S = c->S;
+    d.log2S = c->log2S;
+    d.nboxes = c->nboxes;
+    d.nsc = c->nsc;
+    d.nspecies = (int)c->sp.size();
+    d.nlists = c->nlists;
+    d.dt = (float)c->dt;
+    for (int a = 0; a < 3; ++a)
+        d.move[a] = (float)(c->dt / c->h[a]);
+    d.boxes = c->boxes_d;
+    d.sc_box = c->sc_box_d;
+    d.items = c->items_d;
+    const double V = c->h[0] * c->h[1] * c->h[2];
+    for (size_t s = 0; s < c->sp.size(); ++s) {
+        const pic_species& p = c->sp[s];
+        SpeciesDev& q = d.sp[s];
+        q.eps = (float)(p.charge * c->dt / (2.0 * p.mass));
+        for (int a = 0; a < 3; ++a)
+            q.jcoef[a] = (float)(-p.charge * c->h[a] / (V * c->dt));
+        q.q = (float)p.charge;
+        q.m = (float)p.mass;
+        q.shape = p.shape;
+        q.mobile = p.mobile;
+        float jmax = std::max({std::fabs(q.jcoef[0]), std::fabs(q.jcoef[1]), std::fabs(q.jcoef[2])});
+        q.cbound = jmax * c->wmax[s] * 1.0001f;  // headroom for FP32 rounding
+    }
+    d.cell = c->cell;
+    d.ox = c->ox;
+    d.oy = c->oy;
+    d.oz = c->oz;
+    d.ux = c->ux;
+    d.uy = c->uy;
+    d.uz = c->uz;
+    d.w = c->w;
+    d.pid = c->pid;
+    d.count = c->count;
+    d.nframes = c->nframes;
+    d.foff = c->foff[parity];
+    d.ftab = c->ftab[parity];
+    d.foff_next = c->foff[parity ^ 1];
+    d.ftab_next = c->ftab[parity ^ 1];
+    d.narrive = c->narrive;
+    d.abase = c->abase;
+    d.free_stack = c->free_stack;
+    d.free_top = c->free_top;
+    d.released = c->released;
+    d.pool_frames = (int)c->pool_cap;
+    d.mv_cap = c->mv_cap;
+    d.mv_count = c->mv_count;
+    d.mv_dest = c->mv_dest;
+    d.mv_rank = c->mv_rank;
+    d.mv_cell = c->mv_cell;
+    d.mv_ox = c->mv_ox;
+    d.mv_oy = c->mv_oy;
+    d.mv_oz = c->mv_oz;
+    d.mv_ux = c->mv_ux;
+    d.mv_uy = c->mv_uy;
+    d.mv_uz = c->mv_uz;
+    d.mv_w = c->mv_w;
+    d.mv_pid = c->mv_pid;
+    d.blk_sums = c->blk_sums;
+    d.blk_offs = c->blk_offs;
+    d.totals = c->totals;
+    d.work_counter = c->work_counter;
+    d.status = c->status_d;
+    d.wmax_bits = c->wmax_bits;
+    return d;
+}
+
+template <class T>
+pic_status grow_copy(pic_ctx* c, T** arr, int64_t old_n, int64_t new_n)
+{
+    T* p = nullptr;
+    CKS(dalloc(c, &p, new_n, false));
+    if (*arr && old_n > 0)
+        CK(cudaMemcpyAsync(p, *arr, sizeof(T) * old_n, cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    raw_free(c, *arr);
+    *arr = p;
+    return PIC_OK;
+}
+
+pic_status read_free_top(pic_ctx* c, int* top)
+{
+    CK(cudaMemcpyAsync(top, c->free_top, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return PIC_OK;
+}
+
+// Grow the frame pool to at least `frames` frames, keeping every frame's
+// contents and the free stack.
+pic_status ensure_pool(pic_ctx* c, int64_t frames)
+{
+    if (frames <= c->pool_cap)
+        return PIC_OK;
+    int64_t new_cap = std::max<int64_t>(frames, c->pool_cap + c->pool_cap / 2);
+    if (new_cap * (int64_t)c->S >= (int64_t)1 << 40 || new_cap >= ((int64_t)1 << 31) - 1)
+        return fail(c, PIC_ERR_OOM, "frame pool of %lld frames is too large", (long long)new_cap);
+    destroy_graphs(c);
+    int top = 0;
+    if (c->pool_cap > 0)
+        CKS(read_free_top(c, &top));
+    const int64_t oldS = c->pool_cap * c->S, newS = new_cap * c->S;
+    CKS(grow_copy(c, &c->cell, oldS, newS));
+    CKS(grow_copy(c, &c->ox, oldS, newS));
+    CKS(grow_copy(c, &c->oy, oldS, newS));
+    CKS(grow_copy(c, &c->oz, oldS, newS));
+    CKS(grow_copy(c, &c->ux, oldS, newS));
+    CKS(grow_copy(c, &c->uy, oldS, newS));
+    CKS(grow_copy(c, &c->uz, oldS, newS));
+    CKS(grow_copy(c, &c->w, oldS, newS));
+    if (c->opt.track_ids)
+        CKS(grow_copy(c, &c->pid, oldS, newS));
+    // frame tables: both parities hold at most every frame of the pool
+    CKS(grow_copy(c, &c->ftab[0], c->pool_cap, new_cap));
+    CKS(grow_copy(c, &c->ftab[1], c->pool_cap, new_cap));
+    CKS(grow_copy(c, &c->released, 0, new_cap));
+    // free stack: keep [0, top), push the new frames
+    CKS(grow_copy(c, &c->free_stack, top, new_cap));
+    std::vector<int> fresh((size_t)(new_cap - c->pool_cap));
+    for (size_t i = 0; i < fresh.size(); ++i)
+        fresh[i] = (int)(new_cap - 1 - (int64_t)i);
+    CK(cudaMemcpyAsync(c->free_stack + top, fresh.data(), sizeof(int) * fresh.size(),
+                       cudaMemcpyHostToDevice, c->stream));
+    int new_top = top + (int)fresh.size();
+    CK(cudaMemcpyAsync(c->free_top, &new_top, sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->pool_cap = new_cap;
+    return PIC_OK;
+}
+
+// Capacity of the buffer of particles that change supercell (also the load
+// staging of converted particles).  Its contents never outlive a step.
+pic_status ensure_mv(pic_ctx* c, int64_t cap)
+{
+    if (cap <= c->mv_cap)
+        return PIC_OK;
+    if (cap > INT32_MAX / 2)
+        cap = INT32_MAX / 2;
+    destroy_graphs(c);
+    CK(cudaStreamSynchronize(c->stream));
+    int** ints[] = {&c->mv_dest, &c->mv_rank, &c->mv_cell};
+    float** floats[] = {&c->mv_ox, &c->mv_oy, &c->mv_oz, &c->mv_ux, &c->mv_uy, &c->mv_uz, &c->mv_w};
+    for (auto p : ints) {
+        raw_free(c, *p);
+        *p = nullptr;
+        CKS(dalloc(c, p, cap, false));
+    }
+    for (auto p : floats) {
+        raw_free(c, *p);
+        *p = nullptr;
+        CKS(dalloc(c, p, cap, false));
+    }
+    if (c->opt.track_ids) {
+        raw_free(c, c->mv_pid);
+        c->mv_pid = nullptr;
+        CKS(dalloc(c, &c->mv_pid, cap, false));
+    }
+    c->mv_cap = (int)cap;
+    return PIC_OK;
+}
+
+cudaError_t record(cudaEvent_t e, cudaStream_t s, bool external)
+{
+    return external ? cudaEventRecordWithFlags(e, s, cudaEventRecordExternal) : cudaEventRecord(e, s);
+}
+
+pic_status enqueue_step_mixed(pic_ctx* c, int parity, cudaEvent_t* ev, bool external = false)
+{
+    StepDev d = make_step(c, parity);
+    if (ev)
+        CK(record(ev[0], c->stream, external));
+    CK(cudaMemsetAsync(c->work_counter, 0, sizeof(int), c->stream));
+    CK(cudaMemsetAsync(c->J_all, 0, sizeof(float) * c->field_floats, c->stream));
+    CK(launch_push_deposit(d, c->threads, c->push_grid, c->stream));
+    if (ev)
+        CK(record(ev[1], c->stream, external));
+    CK(launch_frame_plan(d, c->stream));
+    CK(launch_frame_apply(d, 4 * c->nsm, c->stream));
+    if (ev)
+        CK(record(ev[2], c->stream, external));
+    YeePlan yp{c->boxes_d, c->yee_off_d, c->nboxes, c->yee_nblocks, (float)c->dt,
+               {(float)(1.0 / c->h[0]), (float)(1.0 / c->h[1]), (float)(1.0 / c->h[2])}};
+    CK(launch_yee_mixed_plan(yp, c->stream));
+    if (ev)
+        CK(record(ev[3], c->stream, external));
+    return PIC_OK;
+}
+
+// Before the first step: room in the frame pool for one step of growth,
+// a move buffer sized for the particle count.
+pic_status prepare_mixed(pic_ctx* c)
+{
+    if (c->prepared)
+        return PIC_OK;
+    int top = 0;
+    CKS(read_free_top(c, &top));
+    c->frames_used = c->pool_cap - top;
+    int64_t want = c->opt.pool_frames > 0
+                       ? c->opt.pool_frames
+                       : c->frames_used + c->frames_used / 4 + c->nlists / 4 + 1024;
+    CKS(ensure_pool(c, want));
+    int64_t mv = c->opt.move_capacity > 0 ? c->opt.move_capacity
+                                          : std::max<int64_t>(1 << 20, c->total_particles / 6);
+    CKS(ensure_mv(c, mv));
+    int per_sm = 0;
+    CK(configure_push(c->LX, c->LY, c->LZ, c->threads, &per_sm));
+    c->push_grid = std::max(1, per_sm) * c->nsm;
+    c->prepared = true;
+    return PIC_OK;
+}
+
+// Capture one step per frame-table parity.  Any failure leaves the context
+// on eager launches (same kernels, same order).
+pic_status capture_graphs(pic_ctx* c)
+{
+    if (c->gexec[0] || c->graph_failed)
+        return PIC_OK;
+    for (cudaEvent_t& e : c->placeholder)
+        if (!e)
+            CK(cudaEventCreate(&e));
+    for (int p = 0; p < 2; ++p) {
+        cudaGraph_t g = nullptr;
+        if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            cudaGetLastError();
+            c->graph_failed = true;
+            return PIC_OK;
+        }
+        pic_status st = enqueue_step_mixed(c, p, c->placeholder, true);
+        cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+        if (st != PIC_OK) {
+            if (g)
+                cudaGraphDestroy(g);
+            return st;
+        }
+        bool ok = e == cudaSuccess && g;
+        if (ok) {
+            size_t n = 0;
+            ok = cudaGraphGetNodes(g, nullptr, &n) == cudaSuccess;
+            std::vector<cudaGraphNode_t> nodes(n);
+            ok = ok && cudaGraphGetNodes(g, nodes.data(), &n) == cudaSuccess;
+            int found = 0;
+            for (size_t i = 0; ok && i < n; ++i) {
+                cudaGraphNodeType t;
+                if (cudaGraphNodeGetType(nodes[i], &t) != cudaSuccess || t != cudaGraphNodeTypeEventRecord)
+                    continue;
+                cudaEvent_t ev = nullptr;
+                if (cudaGraphEventRecordNodeGetEvent(nodes[i], &ev) != cudaSuccess)
+                    continue;
+                for (int k = 0; k < 4; ++k)
+                    if (ev == c->placeholder[k]) {
+                        c->evnode[p][k] = nodes[i];
+                        ++found;
+                    }
+            }
+            ok = ok && found == 4 && cudaGraphInstantiate(&c->gexec[p], g, 0) == cudaSuccess;
+        }
+        if (!ok) {
+            cudaGetLastError();
+            if (g)
+                cudaGraphDestroy(g);
+            destroy_graphs(c);
+            c->graph_failed = true;
+            return PIC_OK;
+        }
+        c->graph[p] = g;
+    }
+    return PIC_OK;
+}
+
+pic_status launch_graph(pic_ctx* c, int p, cudaEvent_t* ev)
+{
+    for (int k = 0; k < 4; ++k)
+        CK(cudaGraphExecEventRecordNodeSetEvent(c->gexec[p], c->evnode[p][k], ev ? ev[k] : c->placeholder[k]));
+    CK(cudaGraphLaunch(c->gexec[p], c->stream));
+    return PIC_OK;
+}
+
+// ------------------------------------------------------------ stage timing
+
+pic_status harvest_events(pic_ctx* c)
+{
+    if (c->ev_steps == 0)
+        return PIC_OK;
+    CK(cudaStreamSynchronize(c->stream));
+    for (int64_t s = 0; s < c->ev_steps; ++s) {
+        cudaEvent_t* e = &c->events[(size_t)s * 4];
+        float a = 0, b = 0, d = 0, t = 0;
+        CK(cudaEventElapsedTime(&a, e[0], e[1]));
+        CK(cudaEventElapsedTime(&b, e[1], e[2]));
+        CK(cudaEventElapsedTime(&d, e[2], e[3]));
+        CK(cudaEventElapsedTime(&t, e[0], e[3]));
+        c->acc_ms[0] += a;
+        c->acc_ms[1] += b;
+        c->acc_ms[2] += d;
+        c->acc_ms[3] += t;
+        c->timed_steps += 1;
+    }
+    c->ev_steps = 0;
+    return PIC_OK;
+}
+
+pic_status step_events(pic_ctx* c, cudaEvent_t** out)
+{
+    const int64_t kMaxPending = 512;
+    if (c->ev_steps >= kMaxPending)
+        CKS(harvest_events(c));
+    size_t need = (size_t)(c->ev_steps + 1) * 4;
+    while (c->events.size() < need) {
+        cudaEvent_t e;
+        CK(cudaEventCreate(&e));
+        c->events.push_back(e);
+    }
+    *out = &c->events[(size_t)c->ev_steps * 4];
+    c->ev_steps += 1;
+    return PIC_OK;
+}
+
+// ------------------------------------------------------------ plain form
+
+pic_status plain_grow(pic_ctx* c, PlainSpecies& s, int64_t need)
+{
+    if (need <= s.cap)
+        return PIC_OK;
+    int64_t cap = std::max<int64_t>(need, s.cap + s.cap / 2);
+    double** arrs[] = {&s.x, &s.y, &s.z, &s.ux, &s.uy, &s.uz, &s.w};
+    for (auto a : arrs)
+        CKS(grow_copy(c, a, s.n, cap));
+    if (c->opt.track_ids)
+        CKS(grow_copy(c, &s.pid, s.n, cap));
+    s.cap = cap;
+    return PIC_OK;
+}
+
+PlainPushArgs plain_args(const pic_ctx* c, int box, int species)
+{
+    const pic_grid& g = c->grids[box];
+    const PlainBox& b = c->pboxes[box];
+    const PlainSpecies& s = b.sp[species];
+    const pic_species& p = c->sp[species];
+    PlainPushArgs a{};
+    a.nx = g.nx;
+    a.ny = g.ny;
+    a.nz = g.nz;
+    a.n = s.n;
+    a.E = b.E;
+    a.B = b.B;
+    a.J = b.J;
+    a.x = s.x;
+    a.y = s.y;
+    a.z = s.z;
+    a.ux = s.ux;
+    a.uy = s.uy;
+    a.uz = s.uz;
+    a.w = s.w;
+    const double V = c->h[0] * c->h[1] * c->h[2];
+    a.eps = p.charge * c->dt / (2.0 * p.mass);
+    for (int d = 0; d < 3; ++d) {
+        a.jcoef[d] = -p.charge * c->h[d] / (V * c->dt);
+        a.move[d] = c->dt / c->h[d];
+    }
+    a.status = c->status_d;
+    return a;
+}
+
+PlainYeeArgs plain_yee_args(const pic_ctx* c, int box)
+{
+    const pic_grid& g = c->grids[box];
+    const PlainBox& b = c->pboxes[box];
+    PlainYeeArgs a{};
+    a.nx = g.nx;
+    a.ny = g.ny;
+    a.nz = g.nz;
+    a.E = b.E;
+    a.B = b.B;
+    a.J = b.J;
+    for (int d = 0; d < 3; ++d)
+        a.ih[d] = 1.0 / c->h[d];
+    return a;
+}
+
+pic_status enqueue_step_plain(pic_ctx* c, cudaEvent_t* ev)
+{
+    if (ev)
+        CK(cudaEventRecord(ev[0], c->stream));
+    for (int b = 0; b < c->nboxes; ++b) {
+        const pic_grid& g = c->grids[b];
+        int64_t nc = (int64_t)g.nx * g.ny * g.nz;
+        CK(cudaMemsetAsync(c->pboxes[b].J, 0, sizeof(double) * 3 * nc, c->stream));
+        for (size_t s = 0; s < c->sp.size(); ++s)
+            if (c->sp[s].mobile)
+                CK(launch_plain_push(plain_args(c, b, (int)s), c->sp[s].shape, c->stream));
+    }
+    if (ev) {
+        CK(cudaEventRecord(ev[1], c->stream));
+        CK(cudaEventRecord(ev[2], c->stream));
+    }
+    for (int b = 0; b < c->nboxes; ++b)
+        CK(launch_plain_yee(plain_yee_args(c, b), c->dt, c->stream));
+    if (ev)
+        CK(cudaEventRecord(ev[3], c->stream));
+    return PIC_OK;
+}
+
+bool valid_box(const pic_ctx* c, int box) { return box >= 0 && box < c->nboxes; }
+
+int ilog2(int v)
+{
+    int r = 0;
+    while ((1 << r) < v)
+        ++r;
+    return r;
+}
+
+}  // namespace
+
+// ============================================================ C ABI
+
+extern "C" {
+
+pic_status pic_create(const pic_grid* grids, int32_t nboxes, const double dx[3], double dt,
+                      const pic_species* sp, int32_t nspecies, const pic_options* opt,
+                      pic_ctx** out)
+{
+    if (!out)
+        return PIC_ERR_ARG;
+    *out = nullptr;
+    if (!grids || nboxes < 1 || !dx || !sp || nspecies < 1 || nspecies > kMaxSpecies)
+        return PIC_ERR_ARG;
+    if (!(dt > 0.0) || !std::isfinite(dt))
+        return PIC_ERR_ARG;
+    for (int a = 0; a < 3; ++a)
+        if (!(dx[a] > 0.0) || !std::isfinite(dx[a]))
+            return PIC_ERR_ARG;
+    for (int b = 0; b < nboxes; ++b)
+        if (grids[b].nx < 4 || grids[b].ny < 4 || grids[b].nz < 4)
+            return PIC_ERR_ARG;
+    for (int s = 0; s < nspecies; ++s)
+        if (!(sp[s].mass > 0.0) || !std::isfinite(sp[s].charge) || (sp[s].shape != 1 && sp[s].shape != 2))
+            return PIC_ERR_ARG;
+    // no particle may cross half a cell per step (|v| < c), and the Yee
+    // scheme must be stable
+    const double courant = 1.0 / std::sqrt(1.0 / (dx[0] * dx[0]) + 1.0 / (dx[1] * dx[1]) +
+                                           1.0 / (dx[2] * dx[2]));
+    if (!(dt < 0.5 * std::min({dx[0], dx[1], dx[2]})) || !(dt < courant))
+        return PIC_ERR_CFL;
+
+    pic_ctx* c = new (std::nothrow) pic_ctx();
+    if (!c)
+        return PIC_ERR_OOM;
+    pic_options o{};
+    if (opt)
+        o = *opt;
+    c->opt = o;
+    c->precision = o.precision;
+    c->grids.assign(grids, grids + nboxes);
+    c->nboxes = nboxes;
+    for (int a = 0; a < 3; ++a)
+        c->h[a] = dx[a];
+    c->dt = dt;
+    c->sp.assign(sp, sp + nspecies);
+    c->rho_bg.assign(nboxes, 0.0);
+    c->id_next.assign((size_t)nboxes * nspecies, 0);
+    if (c->precision != PIC_PRECISION_FP64_PLAIN && c->precision != PIC_PRECISION_MIXED) {
+        delete c;
+        return PIC_ERR_ARG;
+    }
+
+    auto bail = [&](pic_status st) {
+        pic_destroy(c);
+        return st;
+    };
+    if (cudaGetDevice(&c->device) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(PIC_ERR_CUDA);
+    }
+    cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->device);
+    int optin = 0;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
+    c->smem_optin = (size_t)optin;
+    if (o.stream) {
+        c->stream = static_cast<cudaStream_t>(o.stream);
+    } else {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            return bail(PIC_ERR_CUDA);
+        }
+        c->own_stream = true;
+    }
+    if (dalloc(c, &c->status_d, 1) != PIC_OK || dalloc(c, &c->diag_d, 4) != PIC_OK)
+        return bail(PIC_ERR_OOM);
+    int64_t max_cells = 0;
+    for (int b = 0; b < nboxes; ++b)
+        max_cells = std::max<int64_t>(max_cells, (int64_t)grids[b].nx * grids[b].ny * grids[b].nz);
+    if (dalloc(c, &c->rho_d, max_cells, false) != PIC_OK)
+        return bail(PIC_ERR_OOM);
+
+    if (c->precision == PIC_PRECISION_FP64_PLAIN) {
+        c->pboxes.resize(nboxes);
+        for (int b = 0; b < nboxes; ++b) {
+            int64_t nc = (int64_t)grids[b].nx * grids[b].ny * grids[b].nz;
+            PlainBox& pb = c->pboxes[b];
+            if (dalloc(c, &pb.E, 3 * nc) != PIC_OK || dalloc(c, &pb.B, 3 * nc) != PIC_OK ||
+                dalloc(c, &pb.J, 3 * nc) != PIC_OK)
+                return bail(PIC_ERR_OOM);
+            pb.sp.resize(nspecies);
+        }
+    } else {
+        int sc[3] = {o.sc[0], o.sc[1], o.sc[2]};
+        if (sc[0] == 0 && sc[1] == 0 && sc[2] == 0)
+            sc[0] = sc[1] = sc[2] = 4;
+        c->LX = sc[0];
+        c->LY = sc[1];
+        c->LZ = sc[2];
+        c->S = sc[0] * sc[1] * sc[2];
+        c->log2S = ilog2(c->S);
+        c->threads = o.threads_per_sc > 0 ? o.threads_per_sc : (c->S >= 256 ? 256 : 128);
+        if ((1 << c->log2S) != c->S || !push_supported(c->LX, c->LY, c->LZ, c->threads))
+            return bail(PIC_ERR_ARG);
+        if (push_smem_bytes(c->LX, c->LY, c->LZ, c->threads) > c->smem_optin)
+            return bail(PIC_ERR_ARG);
+        // boxes
+        c->boxes_h.resize(nboxes);
+        int64_t floats = 0;
+        int nsc = 0;
+        std::vector<int> yee_off(nboxes + 1, 0);
+        for (int b = 0; b < nboxes; ++b) {
+            const pic_grid& g = grids[b];
+            if (g.nx % c->LX || g.ny % c->LY || g.nz % c->LZ)
+                return bail(PIC_ERR_ARG);
+            BoxDev& bd = c->boxes_h[b];
+            bd.nx = g.nx;
+            bd.ny = g.ny;
+            bd.nz = g.nz;
+            bd.px = g.nx + 4;
+            bd.py = g.ny + 3;
+            bd.pz = g.nz + 3;
+            bd.nscx = g.nx / c->LX;
+            bd.nscy = g.ny / c->LY;
+            bd.nscz = g.nz / c->LZ;
+            bd.sc_base = nsc;
+            nsc += bd.nscx * bd.nscy * bd.nscz;
+            floats += 3 * padded_cells(bd);
+            yee_off[b + 1] = yee_off[b] + ((g.nx + 31) / 32) * ((g.ny + 7) / 8) * g.nz;
+        }
+        c->nsc = nsc;
+        c->nlists = nsc * nspecies;
+        c->field_floats = floats;
+        c->yee_nblocks = yee_off[nboxes];
+        if (dalloc(c, &c->E_all, floats) != PIC_OK || dalloc(c, &c->B_all, floats) != PIC_OK ||
+            dalloc(c, &c->J_all, floats) != PIC_OK)
+            return bail(PIC_ERR_OOM);
+        int64_t off = 0;
+        std::vector<int> sc_box(nsc);
+        for (int b = 0; b < nboxes; ++b) {
+            BoxDev& bd = c->boxes_h[b];
+            bd.E = c->E_all + off;
+            bd.B = c->B_all + off;
+            bd.J = c->J_all + off;
+            off += 3 * padded_cells(bd);
+            for (int i = 0; i < bd.nscx * bd.nscy * bd.nscz; ++i)
+                sc_box[bd.sc_base + i] = b;
+        }
+        std::vector<int> items(nsc);
+        for (int i = 0; i < nsc; ++i)
+            items[i] = i;
+        const int nblk = (c->nlists + 4095) / 4096;
+        if (dalloc(c, &c->boxes_d, nboxes, false) != PIC_OK || dalloc(c, &c->sc_box_d, nsc, false) != PIC_OK ||
+            dalloc(c, &c->items_d, nsc, false) != PIC_OK || dalloc(c, &c->yee_off_d, nboxes + 1, false) != PIC_OK ||
+            dalloc(c, &c->count, c->nlists) != PIC_OK || dalloc(c, &c->nframes, c->nlists) != PIC_OK ||
+            dalloc(c, &c->narrive, c->nlists) != PIC_OK || dalloc(c, &c->abase, c->nlists) != PIC_OK ||
+            dalloc(c, &c->foff[0], c->nlists) != PIC_OK || dalloc(c, &c->foff[1], c->nlists) != PIC_OK ||
+            dalloc(c, &c->free_top, 1) != PIC_OK || dalloc(c, &c->mv_count, 1) != PIC_OK ||
+            dalloc(c, &c->blk_sums, nblk) != PIC_OK || dalloc(c, &c->blk_offs, nblk) != PIC_OK ||
+            dalloc(c, &c->totals, 1) != PIC_OK || dalloc(c, &c->work_counter, 1) != PIC_OK ||
+            dalloc(c, &c->wmax_bits, kMaxSpecies) != PIC_OK)
+            return bail(PIC_ERR_OOM);
+        if (cudaMemcpyAsync(c->boxes_d, c->boxes_h.data(), sizeof(BoxDev) * nboxes,
+                            cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+            cudaMemcpyAsync(c->sc_box_d, sc_box.data(), sizeof(int) * nsc, cudaMemcpyHostToDevice,
+                            c->stream) != cudaSuccess ||
+            cudaMemcpyAsync(c->items_d, items.data(), sizeof(int) * nsc, cudaMemcpyHostToDevice,
+                            c->stream) != cudaSuccess ||
+            cudaMemcpyAsync(c->yee_off_d, yee_off.data(), sizeof(int) * (nboxes + 1),
+                            cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+            cudaStreamSynchronize(c->stream) != cudaSuccess) {
+            cudaGetLastError();
+            return bail(PIC_ERR_CUDA);
+        }
+    }
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(PIC_ERR_CUDA);
+    }
+    *out = c;
+    return PIC_OK;
+}
+
+pic_status pic_set_background(pic_ctx* c, int32_t box, double rho_bg)
+{
+    CKS(check_ctx(c));
+    if (!valid_box(c, box) || !std::isfinite(rho_bg))
+        return fail(c, PIC_ERR_ARG, "bad box or background");
+    c->rho_bg[box] = rho_bg;
+    return PIC_OK;
+}
+
+pic_status pic_load_particles(pic_ctx* c, int32_t box, int32_t species, int64_t n,
+                              const double* x, const double* u, const double* w)
+{
+    CKS(check_ctx(c));
+    if (!valid_box(c, box) || species < 0 || species >= (int)c->sp.size() || n < 0 ||
+        (n > 0 && (!x || !u)))
+        return fail(c, PIC_ERR_ARG, "bad arguments to pic_load_particles");
+    if (n == 0)
+        return PIC_OK;
+    int64_t& idn = c->id_next[(size_t)box * c->sp.size() + species];
+    if (idn + n > INT32_MAX)
+        return fail(c, PIC_ERR_ARG, "more than 2^31 particles in one (box, species)");
+    destroy_graphs(c);
+    const int64_t chunk = std::min<int64_t>(n, 1 << 22);
+    CKS(ensure_stage(c, sizeof(double) * 7 * (size_t)chunk));
+    double* sx = static_cast<double*>(c->stage_d);
+    double* su = sx + 3 * chunk;
+    double* sw = su + 3 * chunk;
+    for (int64_t b0 = 0; b0 < n; b0 += chunk) {
+        const int64_t m = std::min(chunk, n - b0);
+        CK(cudaMemcpyAsync(sx, x + 3 * b0, sizeof(double) * 3 * m, cudaMemcpyHostToDevice, c->stream));
+        CK(cudaMemcpyAsync(su, u + 3 * b0, sizeof(double) * 3 * m, cudaMemcpyHostToDevice, c->stream));
+        if (w)
+            CK(cudaMemcpyAsync(sw, w + b0, sizeof(double) * m, cudaMemcpyHostToDevice, c->stream));
+        if (c->precision == PIC_PRECISION_FP64_PLAIN) {
+            PlainSpecies& s = c->pboxes[box].sp[species];
+            CKS(plain_grow(c, s, s.n + m));
+            const pic_grid& g = c->grids[box];
+            CK(launch_plain_load(m, sx, su, w ? sw : nullptr, g.nx, g.ny, g.nz, s.x + s.n, s.y + s.n,
+                                 s.z + s.n, s.ux + s.n, s.uy + s.n, s.uz + s.n, s.w + s.n,
+                                 s.pid ? s.pid + s.n : nullptr, (int)(idn + b0), c->status_d,
+                                 c->stream));
+            unsigned st = 0;
+            CK(cudaMemcpyAsync(&st, c->status_d, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+            CK(cudaStreamSynchronize(c->stream));
+            if (st) {
+                CK(cudaMemsetAsync(c->status_d, 0, sizeof(unsigned), c->stream));
+                CK(cudaStreamSynchronize(c->stream));
+                return fail(c, PIC_ERR_ARG, "non-finite particle data");
+            }
+            s.n += m;
+        } else {
+            CKS(ensure_mv(c, std::max<int64_t>(c->mv_cap, m)));
+            StepDev d = make_step(c, c->parity);
+            CK(launch_insert_convert(d, box, species, m, sx, su, w ? sw : nullptr, (int)(idn + b0),
+                                     c->stream));
+            int mi = (int)m;
+            CK(cudaMemcpyAsync(c->mv_count, &mi, sizeof(int), cudaMemcpyHostToDevice, c->stream));
+            unsigned st = 0;
+            unsigned wbits[kMaxSpecies];
+            CK(cudaMemcpyAsync(&st, c->status_d, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+            CK(cudaMemcpyAsync(wbits, c->wmax_bits, sizeof(wbits), cudaMemcpyDeviceToHost, c->stream));
+            CK(cudaStreamSynchronize(c->stream));
+            float wm;
+            std::memcpy(&wm, &wbits[species], sizeof(float));
+            if (wm > c->wmax[species]) {
+                c->wmax[species] = wm;  // the push kernels bake the bound in: recapture
+                destroy_graphs(c);
+            }
+            if (st) {
+                CK(cudaMemsetAsync(c->narrive, 0, sizeof(int) * c->nlists, c->stream));
+                CK(cudaMemsetAsync(c->status_d, 0, sizeof(unsigned), c->stream));
+                CK(cudaMemsetAsync(c->mv_count, 0, sizeof(int), c->stream));
+                CK(cudaStreamSynchronize(c->stream));
+                return fail(c, PIC_ERR_ARG, "non-finite particle data");
+            }
+            // count the frames this insertion needs, grow the pool, then place
+            CK(launch_frame_plan(d, c->stream));
+            int4 tot;
+            int top = 0;
+            CK(cudaMemcpyAsync(&tot, c->totals, sizeof(int4), cudaMemcpyDeviceToHost, c->stream));
+            CKS(read_free_top(c, &top));
+            if (tot.y > top)
+                CKS(ensure_pool(c, (c->pool_cap - top) + tot.y));
+            d = make_step(c, c->parity);
+            CK(launch_frame_apply(d, 4 * c->nsm, c->stream));
+            CKS(status_check(c));
+            c->parity ^= 1;
+        }
+    }
+    idn += n;
+    c->total_particles += n;
+    c->prepared = false;
+    return PIC_OK;
+}
+
+pic_status pic_write_fields(pic_ctx* c, int32_t box, int32_t which, const double* f)
+{
+    CKS(check_ctx(c));
+    if (!valid_box(c, box) || (which != PIC_FIELD_E && which != PIC_FIELD_B) || !f)
+        return fail(c, PIC_ERR_ARG, "bad arguments to pic_write_fields");
+    const pic_grid& g = c->grids[box];
+    const int64_t nc = (int64_t)g.nx * g.ny * g.nz;
+    if (c->precision == PIC_PRECISION_FP64_PLAIN) {
+        double* dst = which == PIC_FIELD_E ? c->pboxes[box].E : c->pboxes[box].B;
+        CK(cudaMemcpyAsync(dst, f, sizeof(double) * 3 * nc, cudaMemcpyHostToDevice, c->stream));
+    } else {
+        CKS(ensure_stage(c, sizeof(double) * 3 * nc));
+        CK(cudaMemcpyAsync(c->stage_d, f, sizeof(double) * 3 * nc, cudaMemcpyHostToDevice, c->stream));
+        CK(launch_fields_to_padded(c->boxes_h[box], which, static_cast<double*>(c->stage_d),
+                                   c->stream));
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    return PIC_OK;
+}
+
+pic_status pic_step_async(pic_ctx* c, int32_t nsteps)
+{
+    CKS(check_ctx(c));
+    if (nsteps < 0)
+        return fail(c, PIC_ERR_ARG, "nsteps < 0");
+    if (c->precision == PIC_PRECISION_FP64_PLAIN) {
+        for (int i = 0; i < nsteps; ++i) {
+            cudaEvent_t* ev = nullptr;
+            if (c->timing)
+                CKS(step_events(c, &ev));
+            CKS(enqueue_step_plain(c, ev));
+        }
+        return PIC_OK;
+    }
+    CKS(prepare_mixed(c));
+    if (c->opt.use_graph)
+        CKS(capture_graphs(c));
+    for (int i = 0; i < nsteps; ++i) {
+        cudaEvent_t* ev = nullptr;
+        if (c->timing)
+            CKS(step_events(c, &ev));
+        if (c->opt.use_graph && c->gexec[c->parity])
+            CKS(launch_graph(c, c->parity, ev));
+        else
+            CKS(enqueue_step_mixed(c, c->parity, ev));
+        c->parity ^= 1;
+    }
+    return PIC_OK;
+}
+
+pic_status pic_sync(pic_ctx* c)
+{
+    CKS(check_ctx(c));
+    return status_check(c);
+}
+
+pic_status pic_step(pic_ctx* c, int32_t nsteps)
+{
+    CKS(pic_step_async(c, nsteps));
+    return pic_sync(c);
+}
+
+pic_status pic_count_particles(pic_ctx* c, int32_t box, int32_t species, int64_t* n_out)
+{
+    CKS(check_ctx(c));
+    if (!valid_box(c, box) || species < 0 || species >= (int)c->sp.size() || !n_out)
+        return fail(c, PIC_ERR_ARG, "bad arguments to pic_count_particles");
+    if (c->precision == PIC_PRECISION_FP64_PLAIN) {
+        *n_out = c->pboxes[box].sp[species].n;
+        return PIC_OK;
+    }
+    const BoxDev& b = c->boxes_h[box];
+    const int nscb = b.nscx * b.nscy * b.nscz;
+    std::vector<int> cnt(nscb);
+    CK(cudaMemcpyAsync(cnt.data(), c->count + (size_t)species * c->nsc + b.sc_base, sizeof(int) * nscb,
+                       cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    int64_t t = 0;
+    for (int v : cnt)
+        t += v;
+    *n_out = t;
+    return PIC_OK;
+}
+
+pic_status pic_read_particles(pic_ctx* c, int32_t box, int32_t species, int64_t cap, double* x,
+                              double* u, double* w, int64_t* id, int64_t* n_out)
+{
+    CKS(check_ctx(c));
+    if (!valid_box(c, box) || species < 0 || species >= (int)c->sp.size() || !n_out || cap < 0)
+        return fail(c, PIC_ERR_ARG, "bad arguments to pic_read_particles");
+    if (id && !c->opt.track_ids)
+        return fail(c, PIC_ERR_ARG, "particle ids requested but track_ids is off");
+    CK(cudaStreamSynchronize(c->stream));
+    int64_t n = 0;
+    CKS(pic_count_particles(c, box, species, &n));
+    *n_out = n;
+    if (n > cap)
+        return fail(c, PIC_ERR_ARG, "cap %lld below the particle count %lld", (long long)cap,
+                    (long long)n);
+    if (n == 0)
+        return PIC_OK;
+    CKS(ensure_stage(c, sizeof(double) * 7 * (size_t)n + sizeof(int64_t) * (size_t)n));
+    double* sx = static_cast<double*>(c->stage_d);
+    double* su = sx + 3 * n;
+    double* sw = su + 3 * n;
+    int64_t* sid = reinterpret_cast<int64_t*>(sw + n);
+    if (c->precision == PIC_PRECISION_FP64_PLAIN) {
+        PlainSpecies& s = c->pboxes[box].sp[species];
+        CK(launch_plain_interleave(n, s.x, s.y, s.z, sx, c->stream));
+        CK(launch_plain_interleave(n, s.ux, s.uy, s.uz, su, c->stream));
+        if (x)
+            CK(cudaMemcpyAsync(x, sx, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, c->stream));
+        if (u)
+            CK(cudaMemcpyAsync(u, su, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, c->stream));
+        if (w)
+            CK(cudaMemcpyAsync(w, s.w, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
+        if (id) {
+            std::vector<int> tmp((size_t)n);
+            CK(cudaMemcpyAsync(tmp.data(), s.pid, sizeof(int) * n, cudaMemcpyDeviceToHost, c->stream));
+            CK(cudaStreamSynchronize(c->stream));
+            for (int64_t i = 0; i < n; ++i)
+                id[i] = tmp[(size_t)i];
+        }
+        CK(cudaStreamSynchronize(c->stream));
+        return PIC_OK;
+    }
+    const BoxDev& b = c->boxes_h[box];
+    const int nscb = b.nscx * b.nscy * b.nscz;
+    std::vector<int> cnt(nscb), off(nscb);
+    CK(cudaMemcpyAsync(cnt.data(), c->count + (size_t)species * c->nsc + b.sc_base, sizeof(int) * nscb,
+                       cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    int64_t acc = 0;
+    for (int i = 0; i < nscb; ++i) {
+        off[i] = (int)acc;
+        acc += cnt[i];
+    }
+    CKS(ensure_ioff(c, nscb));
+    CK(cudaMemcpyAsync(c->ioff_d, off.data(), sizeof(int) * nscb, cudaMemcpyHostToDevice, c->stream));
+    StepDev d = make_step(c, c->parity);
+    CK(launch_read_particles(d, b, box, species, c->ioff_d, sx, su, sw, id ? sid : nullptr, c->stream));
+    if (x)
+        CK(cudaMemcpyAsync(x, sx, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, c->stream));
+    if (u)
+        CK(cudaMemcpyAsync(u, su, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, c->stream));
+    if (w)
+        CK(cudaMemcpyAsync(w, sw, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
+    if (id)
+        CK(cudaMemcpyAsync(id, sid, sizeof(int64_t) * n, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return PIC_OK;
+}
+
+pic_status pic_diagnostics(pic_ctx* c, int32_t box, double out[4])
+{
+    CKS(check_ctx(c));
+    if (!valid_box(c, box) || !out)
+        return fail(c, PIC_ERR_ARG, "bad arguments to pic_diagnostics");
+    const double vol = c->h[0] * c->h[1] * c->h[2];
+    const pic_grid& g = c->grids[box];
+    const int64_t nc = (int64_t)g.nx * g.ny * g.nz;
+    if (c->precision == PIC_PRECISION_FP64_PLAIN) {
+        CK(cudaMemsetAsync(c->rho_d, 0, sizeof(double) * nc, c->stream));
+        CK(cudaMemsetAsync(c->diag_d, 0, sizeof(double) * 4, c->stream));
+        PlainYeeArgs ya = plain_yee_args(c, box);
+        CK(launch_plain_diag_fields(ya, c->diag_d, vol, c->stream));
+        for (size_t s = 0; s < c->sp.size(); ++s)
+            CK(launch_plain_diag_particles(plain_args(c, box, (int)s), c->sp[s].shape, c->sp[s].mass,
+                                           c->sp[s].charge, 1.0 / vol, c->rho_d, c->diag_d, c->stream));
+        CK(launch_plain_diag_gauss(ya, c->rho_d, c->rho_bg[box], c->diag_d, c->stream));
+    } else {
+        StepDev d = make_step(c, c->parity);
+        CK(launch_diag_mixed(d, c->boxes_h[box], box, c->rho_bg[box], c->rho_d, c->diag_d, c->h,
+                             c->stream));
+    }
+    CK(cudaMemcpyAsync(out, c->diag_d, sizeof(double) * 4, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    out[2] += c->rho_bg[box] * vol * (double)nc;
+    return PIC_OK;
+}
+
+pic_status pic_read_fields(pic_ctx* c, int32_t box, int32_t which, double* out)
+{
+    CKS(check_ctx(c));
+    if (!valid_box(c, box) || which < PIC_FIELD_E || which > PIC_FIELD_RHO || !out)
+        return fail(c, PIC_ERR_ARG, "bad arguments to pic_read_fields");
+    const pic_grid& g = c->grids[box];
+    const int64_t nc = (int64_t)g.nx * g.ny * g.nz;
+    if (which == PIC_FIELD_RHO) {
+        double tmp[4];
+        CKS(pic_diagnostics(c, box, tmp));
+        CK(cudaMemcpyAsync(out, c->rho_d, sizeof(double) * nc, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        for (int64_t i = 0; i < nc; ++i)
+            out[i] += c->rho_bg[box];
+        return PIC_OK;
+    }
+    if (c->precision == PIC_PRECISION_FP64_PLAIN) {
+        const PlainBox& b = c->pboxes[box];
+        const double* src = which == PIC_FIELD_E ? b.E : (which == PIC_FIELD_B ? b.B : b.J);
+        CK(cudaMemcpyAsync(out, src, sizeof(double) * 3 * nc, cudaMemcpyDeviceToHost, c->stream));
+    } else {
+        CKS(ensure_stage(c, sizeof(double) * 3 * nc));
+        CK(launch_fields_from_padded(c->boxes_h[box], which, static_cast<double*>(c->stage_d),
+                                     c->stream));
+        CK(cudaMemcpyAsync(out, c->stage_d, sizeof(double) * 3 * nc, cudaMemcpyDeviceToHost, c->stream));
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    return PIC_OK;
+}
+
+pic_status pic_stage_timing(pic_ctx* c, int32_t enable)
+{
+    CKS(check_ctx(c));
+    CKS(harvest_events(c));
+    c->timing = enable != 0;
+    for (double& v : c->acc_ms)
+        v = 0.0;
+    c->timed_steps = 0;
+    return PIC_OK;
+}
+
+pic_status pic_stage_times(pic_ctx* c, double ms[4], int64_t* nsteps_out)
+{
+    CKS(check_ctx(c));
+    if (!ms)
+        return fail(c, PIC_ERR_ARG, "ms is NULL");
+    CKS(harvest_events(c));
+    for (int i = 0; i < kStageTimers; ++i)
+        ms[i] = c->acc_ms[i];
+    if (nsteps_out)
+        *nsteps_out = c->timed_steps;
+    return PIC_OK;
+}
+
+pic_status pic_info(pic_ctx* c, int32_t key, int64_t* out)
+{
+    CKS(check_ctx(c));
+    if (!out)
+        return fail(c, PIC_ERR_ARG, "out is NULL");
+    switch (key) {
+    case PIC_INFO_GRAPH_ACTIVE:
+        *out = (c->precision == PIC_PRECISION_MIXED && c->gexec[0] && c->gexec[1]) ? 1 : 0;
+        return PIC_OK;
+    case PIC_INFO_KERNELS_PER_STEP:
+        if (c->precision == PIC_PRECISION_MIXED) {
+            *out = 1 + 2 + 3 + 3;  // push; scan reduce, top; apply, place, free; Yee x3
+        } else {
+            int64_t k = 0;
+            for (int b = 0; b < c->nboxes; ++b) {
+                for (size_t s = 0; s < c->sp.size(); ++s)
+                    k += (c->sp[s].mobile && c->pboxes[b].sp[s].n > 0) ? 1 : 0;
+                k += 3;
+            }
+            *out = k;
+        }
+        return PIC_OK;
+    case PIC_INFO_POOL_FRAMES:
+        *out = c->pool_cap;
+        return PIC_OK;
+    case PIC_INFO_FRAMES_USED: {
+        if (c->precision != PIC_PRECISION_MIXED || c->pool_cap == 0) {
+            *out = 0;
+            return PIC_OK;
+        }
+        int top = 0;
+        CKS(read_free_top(c, &top));
+        *out = c->pool_cap - top;
+        return PIC_OK;
+    }
+    case PIC_INFO_MOVE_CAPACITY:
+        *out = c->mv_cap;
+        return PIC_OK;
+    default:
+        return fail(c, PIC_ERR_ARG, "unknown info key %d", key);
+    }
+}
+
+const char* pic_last_error(const pic_ctx* c)
+{
+    if (!c)
+        return "null context";
+    return c->err.c_str();
+}
+
+void pic_destroy(pic_ctx* c)
+{
+    if (!c)
+        return;
+    if (c->stream)
+        cudaStreamSynchronize(c->stream);
+    destroy_graphs(c);
+    for (cudaEvent_t e : c->events)
+        cudaEventDestroy(e);
+    for (cudaEvent_t e : c->placeholder)
+        if (e)
+            cudaEventDestroy(e);
+    std::vector<void*> all = c->allocs;
+    for (void* p : all)
+        raw_free(c, p);
+    if (c->own_stream && c->stream)
+        cudaStreamDestroy(c->stream);
+    cudaGetLastError();
+    delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,167 @@
+// pic_internal.cuh -- device-side data layout shared by the libpic kernels.
+//
+// Mixed form (int32 cell + FP32 offset particles, FP32 fields):
+//
+//   Fields of a box live in guard-padded arrays, one array per component,
+//   x fastest: padded index = ((z+1)*py + (y+1))*px + (x+1) for the real cell
+//   (x, y, z), with px = nx + 4 (guards: 1 below, 3 above), py = ny + 3,
+//   pz = nz + 3 (1 below, 2 above).  E and B guards hold periodic copies of
+//   the interior (rewritten by every Yee half update); J guards collect
+//   deposits that the Yee E update folds back into the periodic images.  The
+//   padding lets every supercell read its E/B tile and write its J tile as one
+//   regular box, 16-byte aligned along x (supercell edges are multiples of 4).
+//
+//   Particles live in frames (Sec. 2.1): a frame has S slots, S = cells per
+//   supercell; attribute arrays are indexed frame * S + slot.  Each (species,
+//   supercell) pair owns one list of frames; list L = species * nsc + sc.
+//   The frames of list L are ftab[foff[L] + k], k < nframes[L]; its particles
+//   occupy list slots 0 .. count[L]-1 densely (slot p is frame p / S, slot
+//   p % S), so every frame but the last is full.  The paper keeps the frames
+//   of a supercell in a doubly linked list; here the list is an index table
+//   rebuilt every step by a prefix sum, so the push reads it without pointer
+//   chasing.
+//
+//   A particle stores: cell = local cell index inside its supercell
+//   (lx + LX*(ly + LY*lz)), offsets o in [0, 1) per axis, momentum u (FP32),
+//   weight w.  Its global position is (supercell origin + local cell + o).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace pic {
+
+constexpr int kMaxSpecies = 8;
+
+// Device status word bits (OR-ed by kernels, read by the host after a step).
+enum : unsigned {
+    ST_FRAME_POOL = 1u,  // frame pool exhausted
+    ST_CAPACITY = 2u,    // buffer of particles changing supercell overflowed
+    ST_PARTICLE = 4u,    // non-finite momentum or a move of half a cell or more
+    ST_TIMEOUT = 8u,     // a bounded device wait gave up
+};
+
+struct SpeciesDev {
+    float eps;        // q dt / (2 m)   (Boris half kick factor)
+    float jcoef[3];   // -q h_d / (V dt) (Esirkepov current factor; times w)
+    float q;
+    float m;
+    int shape;        // 1 CIC, 2 TSC
+    int mobile;
+    float cbound;     // max over d of |jcoef[d]| * max weight: bounds |q w P T| / (V dt) terms
+    int pad;
+};
+
+struct BoxDev {
+    int nx, ny, nz;
+    int px, py, pz;           // padded extents
+    int nscx, nscy, nscz;     // supercells per axis
+    int sc_base;              // first global supercell id of the box
+    float* E;                 // 3 * px*py*pz, component-major
+    float* B;
+    float* J;
+};
+
+// Everything the mixed-form step kernels need, passed by value.
+struct StepDev {
+    // geometry
+    int LX, LY, LZ, S, log2S;  // supercell edges, frame size
+    int nboxes, nsc, nspecies, nlists;
+    float dt;
+    float move[3];            // dt / h_d
+    const BoxDev* boxes;      // [nboxes]
+    const int* sc_box;        // [nsc] box of each global supercell
+    const int* items;         // [nsc] supercells in work order
+    SpeciesDev sp[kMaxSpecies];
+    // particle pool
+    int* cell;
+    float* ox;
+    float* oy;
+    float* oz;
+    float* ux;
+    float* uy;
+    float* uz;
+    float* w;
+    int* pid;                 // null unless ids are tracked
+    // lists
+    int* count;               // [nlists]
+    int* nframes;             // [nlists]
+    const int* foff;          // [nlists] frame-table offsets (current)
+    const int* ftab;          // frame table (current)
+    int* foff_next;           // [nlists] (next step's table)
+    int* ftab_next;
+    int* narrive;             // [nlists] arrivals in this step
+    int* abase;               // [nlists] first slot of this step's arrivals
+    // frame pool free stack
+    int* free_stack;          // [pool_frames]
+    int* free_top;            // device scalar
+    int* released;            // [pool_frames] frames released this step
+    int pool_frames;
+    // particles changing supercell this step (SoA, capacity mv_cap)
+    int mv_cap;
+    int* mv_count;            // device scalar
+    int* mv_dest;
+    int* mv_rank;
+    int* mv_cell;
+    float* mv_ox;
+    float* mv_oy;
+    float* mv_oz;
+    float* mv_ux;
+    float* mv_uy;
+    float* mv_uz;
+    float* mv_w;
+    int* mv_pid;
+    // scan scratch
+    int4* blk_sums;           // [scan blocks]
+    int4* blk_offs;           // [scan blocks]
+    int4* totals;             // device scalar: frames, alloc, release, -
+    int* work_counter;        // persistent-kernel work counter
+    unsigned* status;         // device status word
+    unsigned* wmax_bits;      // [kMaxSpecies] float bits of the largest |weight| loaded
+};
+
+// ---------------------------------------------------------------- helpers
+
+__host__ __device__ inline int64_t padded_index(const BoxDev& b, int x, int y, int z)
+{
+    return ((int64_t)(z + 1) * b.py + (y + 1)) * b.px + (x + 1);
+}
+
+__host__ __device__ inline int64_t padded_cells(const BoxDev& b)
+{
+    return (int64_t)b.px * b.py * b.pz;
+}
+
+}  // namespace pic
+
+// Launch helpers implemented in the kernel translation units.
+namespace pic {
+struct YeePlan {
+    const BoxDev* boxes;  // device table
+    const int* blk_off;   // device [nboxes + 1] block offsets
+    int nboxes;
+    int nblocks;
+    float dt;
+    float ih[3];
+};
+cudaError_t configure_push(int LX, int LY, int LZ, int threads, int* per_sm);
+cudaError_t launch_push_deposit(const StepDev& d, int threads, int grid, cudaStream_t st);
+int push_supported(int LX, int LY, int LZ, int threads);
+size_t push_smem_bytes(int LX, int LY, int LZ, int threads);
+int frame_scan_blocks(int nlists);
+cudaError_t launch_frame_plan(const StepDev& d, cudaStream_t st);
+cudaError_t launch_frame_apply(const StepDev& d, int place_blocks, cudaStream_t st);
+cudaError_t launch_insert_convert(const StepDev& d, int box, int species, int64_t n,
+                                  const double* x, const double* u, const double* w,
+                                  int id_base, cudaStream_t st);
+cudaError_t launch_read_particles(const StepDev& d, const BoxDev& hb, int box, int species,
+                                  const int* list_off, double* x, double* u, double* w,
+                                  int64_t* id, cudaStream_t st);
+cudaError_t launch_yee_mixed_plan(const YeePlan& p, cudaStream_t st);
+cudaError_t launch_fields_to_padded(const BoxDev& b, int which, const double* src,
+                                    cudaStream_t st);
+cudaError_t launch_fields_from_padded(const BoxDev& b, int which, double* dst, cudaStream_t st);
+cudaError_t launch_diag_mixed(const StepDev& d, const BoxDev& hb, int box, double rho_bg,
+                              double* rho_scratch, double* out, const double h[3],
+                              cudaStream_t st);
+}  // namespace pic

@@ -166,6 +166,31 @@ def thermal_tsc(n=256, ppc=8, u_th=0.05, seed_offset=1, ny=None, nz=None) -> Wor
                     steps=200)
 
 
+def fill_thermal(x, u, w, nx, ny, nz, ppc, u_th, dens=0.01, seed_offset=1, slab=8):
+    """Write the thermal_tsc recipe (ppc uniform positions per cell,
+    Maxwellian u_th, weight dens / ppc) into preallocated (n,3), (n,3), (n,)
+    float64 arrays, one z-slab at a time with its own PCG64 stream, so that a
+    256^3 state (134M particles) never needs more than the output arrays.
+    Returns the particle count written."""
+    per_layer = nx * ny * ppc
+    k = 0
+    for z0 in range(0, nz, slab):
+        z1 = min(nz, z0 + slab)
+        rng = np.random.default_rng([BASE_SEED + seed_offset, z0])
+        cz, cy, cx = np.meshgrid(np.arange(z0, z1), np.arange(ny), np.arange(nx), indexing="ij")
+        m = (z1 - z0) * per_layer
+        xs = x[k:k + m]
+        xs[:, 0] = np.repeat(cx.ravel(), ppc)
+        xs[:, 1] = np.repeat(cy.ravel(), ppc)
+        xs[:, 2] = np.repeat(cz.ravel(), ppc)
+        xs += rng.random((m, 3))
+        u[k:k + m] = rng.normal(0.0, u_th, size=(m, 3))
+        w[k:k + m] = dens / ppc
+        k += m
+    np.minimum(x[:k], np.array([nx, ny, nz], dtype=np.float64) * (1.0 - 2.0 ** -52), out=x[:k])
+    return k
+
+
 def laser_ramp(nx=128, ny=1024, nz=128, ppc=4, seed_offset=2, lam=32.0, a0=3.0, waist=16.0,
                duration=40.0, y_c=80.0, ramp=(160, 360), n_frac=0.01) -> Workload:
     """Electron + proton species, ppc each, density rising linearly from 0 at
