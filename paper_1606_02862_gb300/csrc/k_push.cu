@@ -25,17 +25,20 @@
 //
 // Particles are staged a chunk at a time in shared memory (coalesced loads
 // and stores) and pushed in the order of a counting sort by nearest node, so
-// the lanes of a warp read neighbouring field words and add to neighbouring
-// current words.  The current tile accumulates in fixed point (see fx_add).
+// the lanes of a warp read neighbouring field words (shared-memory
+// broadcasts).  The push writes a deposit record per particle; the deposit
+// then runs in a lane order whose neighbours are C/32 sorted positions apart,
+// so one warp's atomics land on different nodes.  The current of a chunk
+// accumulates in fixed point (see chunk_scale).
 // Two deposit paths, both exact forms of that formula:
 //   common: on every axis the old and the new position round to the same
 //     node (TSC) / stay in the same cell (CIC), so the union of the two
 //     supports is 3 (TSC) / 2 (CIC) nodes and DS has closed per-node forms
 //     in the displacement D (no cancellation in FP32); 54 (TSC) / 12 (CIC)
 //     shared atomics, no branches;
-//   queued: the rest (a few percent of particles) wait in a shared queue and
-//     are deposited with the general 4-node window by full warps, so the
-//     rare case costs no divergence in the common loop.
+//   general: the rest (a few percent of particles) are listed and deposited
+//     with the general 4-node window in a loop of their own, so the rare
+//     case costs no divergence in the common loop.
 // The shared tiles use an odd row pitch so that the 32 banks spread over
 // neighbouring rows.
 #include "pic_internal.cuh"
@@ -162,58 +165,42 @@ __device__ __forceinline__ float esk_T(float s0e, float dse, float s0f, float ds
 
 // ------------------------------------------------------------ fixed-point J tile
 //
-// The shared J tile accumulates in integers: shared-memory int32 atomics are
-// native and combine lanes that hit one address, where FP32 shared atomics
-// are a compare-and-swap loop that serialises them.  A contribution v (already
-// multiplied by the tile scale s) is split into hi = floor(v) and lo =
-// round((v - hi) 2^m), added to two int32 accumulators; the tile value is
-// (hi_sum 2^m + lo_sum) / (s 2^m).  The scale comes from a bound on every
-// contribution (|P| <= |D| < 1/2, |T| <= 1, |coef w| <= cbound) and on the
-// number of contributions per node (the particles of the supercell), so no
-// accumulator can overflow; the resolution is about 2^-42 of the bound.
-// Conversions use the 1.5 * 2^23 magic-number add (|h|, lo < 2^22).
-struct FxScale {
-    float s;      // multiply a contribution by s to get hi units
-    float two_m;  // 2^m: lo units per hi unit
-    float inv;    // 1 / (s 2^m): back to current density
-};
-
+// The shared J tile accumulates each chunk of particles in int32: shared-
+// memory int32 atomics are native, where FP32 shared atomics are a
+// compare-and-swap loop.  A chunk's contributions are scaled by a power of
+// two chosen from the chunk itself: with B = max over its particles and
+// axes of |jcoef_d w D_d| (|P| <= |D| and |T| <= 1 bound every term of the
+// current by it) and n <= 256 particles, each scaled term is below 2^21 and a
+// node's sum below 2^30, so nothing overflows and a term keeps 2^-22 B
+// resolution.
+// After the chunk the integer tile is folded into an FP32 tile.  Scaled terms
+// convert to integers with the 1.5 * 2^23 magic-number add.
 __device__ __forceinline__ int magic_int(float x)
 {
     return __float_as_int(x + 12582912.0f) - 0x4B400000;
 }
 
-__device__ __forceinline__ void fx_add(int* hi, int* lo, float v, float two_m)
+// scale = 2^(min(21, 30 - ceil(log2 n)) - e) with bound <= 2^e: a scaled
+// term is below 2^21 (magic-number range) and n of them below 2^30
+__device__ __forceinline__ float chunk_scale(int n, float bound, float* inv)
 {
-    const float h = floorf(v);
-    const float l = (v - h) * two_m;
-    atomicAdd(hi, magic_int(h));
-    atomicAdd(lo, magic_int(l));
-}
-
-__device__ __forceinline__ FxScale fx_scale(int ntot, float bound)
-{
-    const int lg = ntot > 1 ? 32 - __clz(ntot - 1) : 0;  // ceil(log2 ntot)
-    const int m = min(22, 30 - lg);
+    const int lg = n > 1 ? 32 - __clz(n - 1) : 0;
     const int hb = min(21, 30 - lg);
     int e = 0;
     if (bound > 0.0f)
-        frexpf(bound, &e);  // bound <= 2^e
-    FxScale f;
-    f.s = ldexpf(1.0f, hb - e);
-    f.two_m = ldexpf(1.0f, m);
-    f.inv = ldexpf(1.0f, e - hb - m);
-    return f;
+        frexpf(bound, &e);
+    *inv = ldexpf(1.0f, e - hb);
+    return ldexpf(1.0f, hb - e);
 }
 
 // Deposit the three current components on a window of M nodes per axis
 // (M-1 half nodes along the current's own axis); node 0 of axis d sits at
-// tile index b[d].  cx..cz carry q w / (V dt) h_d and the tile scale.
+// tile index b[d].  cx..cz carry jcoef_d w times the chunk scale.
 template <int M, int PX, int TY, int NJ>
-__device__ __forceinline__ void deposit_window(int* sJh, int* sJl, const int b[3], const float* S0x,
+__device__ __forceinline__ void deposit_window(int* sJi, const int b[3], const float* S0x,
                                                const float* S0y, const float* S0z, const float* DSx,
                                                const float* DSy, const float* DSz, float cx, float cy,
-                                               float cz, float two_m)
+                                               float cz)
 {
     constexpr int PY = PX * TY;
     {
@@ -227,10 +214,10 @@ __device__ __forceinline__ void deposit_window(int* sJh, int* sJl, const int b[3
 #pragma unroll
             for (int j = 0; j < M; ++j) {
                 const float T = cx * esk_T(S0y[j], DSy[j], S0z[k], DSz[k]);
-                const int row = (b[2] + k) * PY + (b[1] + j) * PX + b[0];
+                int* row = sJi + (b[2] + k) * PY + (b[1] + j) * PX + b[0];
 #pragma unroll
                 for (int i = 0; i < M - 1; ++i)
-                    fx_add(sJh + row + i, sJl + row + i, P[i] * T, two_m);
+                    atomicAdd(row + i, magic_int(P[i] * T));
             }
     }
     {
@@ -244,10 +231,10 @@ __device__ __forceinline__ void deposit_window(int* sJh, int* sJl, const int b[3
 #pragma unroll
             for (int i = 0; i < M; ++i) {
                 const float T = cy * esk_T(S0z[k], DSz[k], S0x[i], DSx[i]);
-                const int col = NJ + (b[2] + k) * PY + b[1] * PX + (b[0] + i);
+                int* col = sJi + NJ + (b[2] + k) * PY + b[1] * PX + (b[0] + i);
 #pragma unroll
                 for (int j = 0; j < M - 1; ++j)
-                    fx_add(sJh + col + j * PX, sJl + col + j * PX, P[j] * T, two_m);
+                    atomicAdd(col + j * PX, magic_int(P[j] * T));
             }
     }
     {
@@ -261,10 +248,10 @@ __device__ __forceinline__ void deposit_window(int* sJh, int* sJl, const int b[3
 #pragma unroll
             for (int i = 0; i < M; ++i) {
                 const float T = cz * esk_T(S0x[i], DSx[i], S0y[j], DSy[j]);
-                const int col = 2 * NJ + b[2] * PY + (b[1] + j) * PX + (b[0] + i);
+                int* col = sJi + 2 * NJ + b[2] * PY + (b[1] + j) * PX + (b[0] + i);
 #pragma unroll
                 for (int k = 0; k < M - 1; ++k)
-                    fx_add(sJh + col + k * PY, sJl + col + k * PY, P[k] * T, two_m);
+                    atomicAdd(col + k * PY, magic_int(P[k] * T));
             }
     }
 }
@@ -338,36 +325,15 @@ struct Stage {
     int perm[C];  // sorted position -> chunk position
 };
 
-// Particles whose move needs the general 4-node window.
+// Deposit inputs of the chunk's moves, by sorted position.
 template <int C>
-struct DepositQueue {
-    int l[C];        // packed local cell coordinates lx | ly << 8 | lz << 16
+struct Records {
+    int l[C];        // packed local cell lx | ly << 8 | lz << 16, bit 24: general window
     float o[3][C];   // old in-cell offsets
     float D[3][C];   // displacement in cells
     float w[C];      // weight
+    int gen[C];      // sorted positions of the moves that need the general window
 };
-
-template <class T, int SHAPE, int C>
-__device__ __forceinline__ void deposit_queued(int* sJh, int* sJl, const DepositQueue<C>& q, int e,
-                                               const float jc[3], const FxScale& fx)
-{
-    const int l = q.l[e];
-    float S0[3][4], DS[3][4];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        const float o = q.o[a][e], D = q.D[a][e];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const float d0 = o - (float)(k - 1);
-            S0[a][k] = SHAPE == 2 ? tsc_S(d0) : cic_S(d0);
-            DS[a][k] = SHAPE == 2 ? tsc_dS(d0, D) : cic_dS(d0, D);
-        }
-    }
-    const int b[3] = {l & 0xff, (l >> 8) & 0xff, l >> 16};  // node l-1 sits at tile index l
-    const float w = q.w[e] * fx.s;
-    deposit_window<4, T::PX, T::TY, T::N>(sJh, sJl, b, S0[0], S0[1], S0[2], DS[0], DS[1], DS[2],
-                                          jc[0] * w, jc[1] * w, jc[2] * w, fx.two_m);
-}
 
 template <class T, int SHAPE>
 struct Keys {
@@ -382,29 +348,95 @@ constexpr int max_keys()
 
 template <class T, int NT>
 struct SharedState {
-    static constexpr int C = 2 * NT;
+    static constexpr int C = 2 * NT < 256 ? 2 * NT : 256;  // chunk: at most 256 particles
     Stage<C> st;
-    DepositQueue<C> q;
+    Records<C> rec;
     int hist[max_keys<T>()];
     int off[max_keys<T>()];
     int holes[kHoleCap];
     int src[kHoleCap];
     int warp[32];
-    int item, any, nq, nholes, nhead, nsrc;
-    FxScale fx;
+    int item, any, ngen, nholes, nhead, nsrc;
+    unsigned bound_bits;  // float bits of the chunk's largest |jcoef w D|
 };
+
+// ------------------------------------------------------------ deposit of one record
+
+// Common window: nodes a-1, a, a+1 (TSC, a = round(o)) or 0, 1 (CIC) on every
+// axis; S0 is the particle's shape there and DS has closed forms in D.
+template <class T, int SHAPE, int C>
+__device__ __forceinline__ void deposit_common(int* sJi, const Records<C>& r, int e, const float jc[3],
+                                               float scale)
+{
+    constexpr int NW = SHAPE == 2 ? 3 : 2;
+    const int l = r.l[e];
+    const int lc[3] = {l & 0xff, (l >> 8) & 0xff, (l >> 16) & 0xff};
+    float S0[3][NW], DS[3][NW];
+    int b[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float o = r.o[a][e], D = r.D[a][e];
+        if (SHAPE == 2) {
+            const bool up = o >= 0.5f;
+            const float di = up ? o - 1.0f : o;
+            b[a] = lc[a] + (up ? 1 : 0);
+            const float lo = 0.5f - di, hi = 0.5f + di;
+            S0[a][0] = 0.5f * lo * lo;
+            S0[a][1] = 0.75f - di * di;
+            S0[a][2] = 0.5f * hi * hi;
+            // DS = -D/2 (1 - d0 - d1), -D (d0 + d1), D/2 (1 + d0 + d1), d1 = d0 + D
+            const float sum = 2.0f * di + D;
+            DS[a][0] = -0.5f * D * (1.0f - sum);
+            DS[a][1] = -D * sum;
+            DS[a][2] = 0.5f * D * (1.0f + sum);
+        } else {
+            b[a] = lc[a] + 1;
+            S0[a][0] = 1.0f - o;
+            S0[a][1] = o;
+            DS[a][0] = -D;
+            DS[a][1] = D;
+        }
+    }
+    const float ws = r.w[e] * scale;
+    deposit_window<NW, T::PX, T::TY, T::N>(sJi, b, S0[0], S0[1], S0[2], DS[0], DS[1], DS[2], jc[0] * ws,
+                                           jc[1] * ws, jc[2] * ws);
+}
+
+// General window: nodes l-1 .. l+2 on every axis.
+template <class T, int SHAPE, int C>
+__device__ __forceinline__ void deposit_general(int* sJi, const Records<C>& r, int e, const float jc[3],
+                                                float scale)
+{
+    const int l = r.l[e];
+    float S0[3][4], DS[3][4];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float o = r.o[a][e], D = r.D[a][e];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float d0 = o - (float)(k - 1);
+            S0[a][k] = SHAPE == 2 ? tsc_S(d0) : cic_S(d0);
+            DS[a][k] = SHAPE == 2 ? tsc_dS(d0, D) : cic_dS(d0, D);
+        }
+    }
+    const int b[3] = {l & 0xff, (l >> 8) & 0xff, (l >> 16) & 0xff};  // node l-1 sits at tile index l
+    const float ws = r.w[e] * scale;
+    deposit_window<4, T::PX, T::TY, T::N>(sJi, b, S0[0], S0[1], S0[2], DS[0], DS[1], DS[2], jc[0] * ws,
+                                          jc[1] * ws, jc[2] * ws);
+}
 
 // ------------------------------------------------------------ one particle
 
-template <class T, int SHAPE, int C>
+template <class T, int SHAPE, int NT>
 __device__ __forceinline__ void push_one(const StepDev& d, const SpeciesDev& sp, int s, const BoxDev& bx,
-                                         int scx, int scy, int scz, const float* sF, int* sJh, int* sJl,
-                                         Stage<C>& st, DepositQueue<C>& q, int& s_nq, int& s_nholes,
-                                         int* s_holes, const FxScale& fx, int j, int p,
+                                         int scx, int scy, int scz, const float* sF,
+                                         SharedState<T, NT>& sh, int j, int p, int sidx,
                                          unsigned& my_status)
 {
     constexpr int LX = T::LX, LY = T::LY, LZ = T::LZ, N = T::N, PX = T::PX, TY = T::TY;
     constexpr int NW = SHAPE == 2 ? 3 : 2;
+    auto& st = sh.st;
+    auto& rec = sh.rec;
     const int cell = st.cell[j];
     const float ox = st.o[0][j], oy = st.o[1][j], oz = st.o[2][j];
     float ux = st.u[0][j], uy = st.u[1][j], uz = st.u[2][j];
@@ -444,51 +476,26 @@ __device__ __forceinline__ void push_one(const StepDev& d, const SpeciesDev& sp,
     }
     const float x1 = ox + Dx, y1 = oy + Dy, z1 = oz + Dz;
 
-    // Esirkepov deposition
+    // deposit record (the current goes in afterwards, in another lane order)
     bool common;
     if (SHAPE == 2)
         common = ((ox >= 0.5f) == (x1 >= 0.5f)) && ((oy >= 0.5f) == (y1 >= 0.5f)) &&
                  ((oz >= 0.5f) == (z1 >= 0.5f));
     else
         common = x1 >= 0.0f && x1 < 1.0f && y1 >= 0.0f && y1 < 1.0f && z1 >= 0.0f && z1 < 1.0f;
-    if (common) {
-        float DSx[NW], DSy[NW], DSz[NW];
-        if (SHAPE == 2) {
-            // nodes a-1, a, a+1 with delta = o - a (d1 = d0 + D):
-            // DS = -D/2 (1 - d0 - d1), -D (d0 + d1), D/2 (1 + d0 + d1)
-            const float Ds[3] = {Dx, Dy, Dz};
-            const float dl[3] = {ax.di, ay.di, az.di};
-            float* out[3] = {DSx, DSy, DSz};
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                const float sum = 2.0f * dl[a] + Ds[a];
-                out[a][0] = -0.5f * Ds[a] * (1.0f - sum);
-                out[a][1] = -Ds[a] * sum;
-                out[a][2] = 0.5f * Ds[a] * (1.0f + sum);
-            }
-        } else {
-            DSx[0] = -Dx;
-            DSx[1] = Dx;
-            DSy[0] = -Dy;
-            DSy[1] = Dy;
-            DSz[0] = -Dz;
-            DSz[1] = Dz;
-        }
-        const int b[3] = {ax.bi, ay.bi, az.bi};
-        const float ws = w * fx.s;
-        deposit_window<NW, PX, TY, N>(sJh, sJl, b, ax.wi, ay.wi, az.wi, DSx, DSy, DSz,
-                                      sp.jcoef[0] * ws, sp.jcoef[1] * ws, sp.jcoef[2] * ws, fx.two_m);
-    } else {
-        const int e = atomicAdd(&s_nq, 1);  // < C: one entry per particle of the chunk
-        q.l[e] = lx | (ly << 8) | (lz << 16);
-        q.o[0][e] = ox;
-        q.o[1][e] = oy;
-        q.o[2][e] = oz;
-        q.D[0][e] = Dx;
-        q.D[1][e] = Dy;
-        q.D[2][e] = Dz;
-        q.w[e] = w;
-    }
+    rec.l[sidx] = lx | (ly << 8) | (lz << 16) | (common ? 0 : (1 << 24));
+    rec.o[0][sidx] = ox;
+    rec.o[1][sidx] = oy;
+    rec.o[2][sidx] = oz;
+    rec.D[0][sidx] = Dx;
+    rec.D[1][sidx] = Dy;
+    rec.D[2][sidx] = Dz;
+    rec.w[sidx] = w;
+    if (!common)
+        rec.gen[atomicAdd(&sh.ngen, 1)] = sidx;
+    const float bnd = fabsf(w) * fmaxf(fmaxf(fabsf(sp.jcoef[0] * Dx), fabsf(sp.jcoef[1] * Dy)),
+                                       fabsf(sp.jcoef[2] * Dz));
+    atomicMax(&sh.bound_bits, __float_as_uint(bnd));
 
     // new cell and offsets
     const float fx_ = floorf(x1), fy_ = floorf(y1), fz_ = floorf(z1);
@@ -536,9 +543,9 @@ __device__ __forceinline__ void push_one(const StepDev& d, const SpeciesDev& sp,
             my_status |= ST_CAPACITY;
         }
         st.cell[j] = -1;
-        const int h = atomicAdd(&s_nholes, 1);
+        const int h = atomicAdd(&sh.nholes, 1);
         if (h < kHoleCap)
-            s_holes[h] = p;
+            sh.holes[h] = p;
     }
 }
 
@@ -547,13 +554,13 @@ __device__ __forceinline__ void push_one(const StepDev& d, const SpeciesDev& sp,
 template <class T, int SHAPE, int NT>
 __device__ __forceinline__ void push_list(const StepDev& d, const SpeciesDev& sp, int s, int g,
                                           const BoxDev& bx, int scx, int scy, int scz,
-                                          const float* sF, int* sJh, int* sJl,
+                                          const float* sF, int* sJi, float* sJf,
                                           SharedState<T, NT>& sh, unsigned& my_status)
 {
-    constexpr int LX = T::LX, LY = T::LY, S = T::S;
+    constexpr int LX = T::LX, LY = T::LY, S = T::S, N = T::N;
     constexpr int C = SharedState<T, NT>::C;
     constexpr int K = Keys<T, SHAPE>::K;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int L = s * d.nsc + g;
     const int n = d.count[L];
     const int* ft = d.ftab + d.foff[L];
@@ -561,6 +568,10 @@ __device__ __forceinline__ void push_list(const StepDev& d, const SpeciesDev& sp
         const int cn = min(C, n - base);
         for (int k = tid; k < K; k += NT)
             sh.hist[k] = 0;
+        if (tid == 0) {
+            sh.ngen = 0;
+            sh.bound_bits = 0u;
+        }
         __syncthreads();
         // stage the chunk (coalesced), key = nearest node (TSC) / cell (CIC)
         for (int j = tid; j < cn; j += NT) {
@@ -596,17 +607,25 @@ __device__ __forceinline__ void push_list(const StepDev& d, const SpeciesDev& sp
             sh.st.perm[sh.off[kr >> 16] + (kr & 0xffff)] = j;
         }
         __syncthreads();
-        // push in sorted order: neighbouring lanes share cells
+        // push in sorted order: neighbouring lanes read neighbouring field words
         for (int sidx = tid; sidx < cn; sidx += NT) {
             const int j = sh.st.perm[sidx];
-            push_one<T, SHAPE, C>(d, sp, s, bx, scx, scy, scz, sF, sJh, sJl, sh.st, sh.q, sh.nq,
-                                  sh.nholes, sh.holes, sh.fx, j, base + j, my_status);
+            push_one<T, SHAPE, NT>(d, sp, s, bx, scx, scy, scz, sF, sh, j, base + j, sidx, my_status);
         }
         __syncthreads();
-        // queued moves with the general window, then write the chunk back
-        const int nq = sh.nq;
-        for (int e = tid; e < nq; e += NT)
-            deposit_queued<T, SHAPE, C>(sJh, sJl, sh.q, e, sp.jcoef, sh.fx);
+        // deposit: lanes take sorted positions C/32 apart, so one warp's
+        // atomics land on different nodes; then the general-window moves
+        float inv;
+        const float scale = chunk_scale(cn, __uint_as_float(sh.bound_bits), &inv);
+        for (int r = 0; r < C / NT; ++r) {
+            const int e = lane * (C / 32) + wid * (C / NT) + r;
+            if (e < cn && !(sh.rec.l[e] >> 24))
+                deposit_common<T, SHAPE, C>(sJi, sh.rec, e, sp.jcoef, scale);
+        }
+        const int ngen = sh.ngen;
+        for (int q = tid; q < ngen; q += NT)
+            deposit_general<T, SHAPE, C>(sJi, sh.rec, sh.rec.gen[q], sp.jcoef, scale);
+        // write the chunk back (coalesced)
         for (int j = tid; j < cn; j += NT) {
             const int p = base + j;
             const int64_t idx = (int64_t)ft[p >> d.log2S] * S + (p & (S - 1));
@@ -622,8 +641,15 @@ __device__ __forceinline__ void push_list(const StepDev& d, const SpeciesDev& sp
             }
         }
         __syncthreads();
-        if (tid == 0)
-            sh.nq = 0;
+        // fold the chunk's integer tile into the FP32 tile
+        for (int v = tid; v < 3 * N; v += NT) {
+            const int q = sJi[v];
+            if (q != 0) {
+                sJf[v] += (float)q * inv;
+                sJi[v] = 0;
+            }
+        }
+        __syncthreads();
     }
 }
 
@@ -715,11 +741,11 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_push_deposit(const StepDev d)
     constexpr int TX = T::TX, TY = T::TY, TZ = T::TZ, PX = T::PX, N = T::N;
     constexpr int LX = T::LX, LY = T::LY, LZ = T::LZ;
     extern __shared__ __align__(16) float smem[];
-    // layout (dyn_smem): [6N field floats][3N hi ints][3N lo ints][SharedState]
-    float* sF = smem;                                     // [6][TZ][TY][PX]: Ex Ey Ez Bx By Bz
-    int* sJh = reinterpret_cast<int*>(smem + 6 * N);      // [3][TZ][TY][PX] hi words
-    int* sJl = sJh + 3 * N;                               // [3][TZ][TY][PX] lo words
-    SharedState<T, NT>& sh = *reinterpret_cast<SharedState<T, NT>*>(sJl + 3 * N);
+    // layout (dyn_smem): [6N field floats][3N int current][3N float current][SharedState]
+    float* sF = smem;                                 // [6][TZ][TY][PX]: Ex Ey Ez Bx By Bz
+    int* sJi = reinterpret_cast<int*>(smem + 6 * N);  // [3][TZ][TY][PX] chunk accumulator
+    float* sJf = smem + 9 * N;                        // [3][TZ][TY][PX] supercell current
+    SharedState<T, NT>& sh = *reinterpret_cast<SharedState<T, NT>*>(smem + 12 * N);
 
     const int tid = threadIdx.x;
     unsigned my_status = 0;
@@ -740,16 +766,12 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_push_deposit(const StepDev d)
 
         if (tid == 0) {
             int ntot = 0;
-            float bound = 0.0f;
             for (int s = 0; s < d.nspecies; ++s) {
                 const int c = d.count[s * d.nsc + g];
-                if (d.sp[s].mobile && c > 0) {
+                if (d.sp[s].mobile && c > 0)
                     ntot += c;
-                    bound = fmaxf(bound, 0.5f * d.sp[s].cbound);
-                }
             }
             sh.any = ntot;
-            sh.fx = fx_scale(ntot, bound);
         }
         __syncthreads();
         if (sh.any == 0) {
@@ -757,7 +779,7 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_push_deposit(const StepDev d)
             continue;
         }
 
-        // ---- 1. stage the E/B tile, zero the J tile
+        // ---- 1. stage the E/B tile, zero the J tiles
         const int64_t pcell = padded_cells(bx);
         const int64_t start = ((int64_t)(scz * LZ) * bx.py + scy * LY) * bx.px + scx * LX;
         constexpr int ROW4 = TX / 4;
@@ -778,9 +800,7 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_push_deposit(const StepDev d)
             dst[3] = val.w;
         }
         for (int v = tid; v < 6 * N; v += NT)
-            sJh[v] = 0;  // hi and lo words are contiguous
-        if (tid == 0)
-            sh.nq = 0;
+            sJi[v] = 0;  // int and float current tiles are contiguous; 0 bits = 0.0f
         __syncthreads();
 
         // ---- 2. particles of every mobile species, 3. compaction
@@ -794,10 +814,9 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_push_deposit(const StepDev d)
                 sh.nholes = 0;
             __syncthreads();
             if (sp.shape == 2)
-                push_list<T, 2, NT>(d, sp, s, g, bx, scx, scy, scz, sF, sJh, sJl, sh, my_status);
+                push_list<T, 2, NT>(d, sp, s, g, bx, scx, scy, scz, sF, sJi, sJf, sh, my_status);
             else
-                push_list<T, 1, NT>(d, sp, s, g, bx, scx, scy, scz, sF, sJh, sJl, sh, my_status);
-            __syncthreads();
+                push_list<T, 1, NT>(d, sp, s, g, bx, scx, scy, scz, sF, sJi, sJf, sh, my_status);
             const int nh = sh.nholes;
             if (nh > 0) {
                 compact_list<T, NT>(d, L, n, nh, sh.holes, sh.src, sh.nhead, sh.nsrc);
@@ -809,26 +828,18 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_push_deposit(const StepDev d)
         }
 
         // ---- 4. add the J tile to global J
-        const FxScale fx = sh.fx;
         constexpr int NJ4 = 3 * TZ * TY * ROW4;
         for (int v = tid; v < NJ4; v += NT) {
             const int r4 = v % ROW4;
             const int row = v / ROW4;
-            const int e = row * PX + 4 * r4;
-            float val[4];
-            bool any = false;
-#pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                const int hi = sJh[e + t], lo = sJl[e + t];
-                any |= (hi | lo) != 0;
-                val[t] = fmaf((float)hi, fx.two_m, (float)lo) * fx.inv;
-            }
-            if (any) {
+            const float* src = sJf + row * PX + 4 * r4;
+            const float4 val = make_float4(src[0], src[1], src[2], src[3]);
+            if (val.x != 0.f || val.y != 0.f || val.z != 0.f || val.w != 0.f) {
                 const int ty = row % TY;
                 const int tz = (row / TY) % TZ;
                 const int c = row / (TY * TZ);
                 float* dst = bx.J + c * pcell + start + ((int64_t)tz * bx.py + ty) * bx.px + 4 * r4;
-                atomicAdd(reinterpret_cast<float4*>(dst), make_float4(val[0], val[1], val[2], val[3]));
+                atomicAdd(reinterpret_cast<float4*>(dst), val);
             }
         }
         __syncthreads();
@@ -842,7 +853,7 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_push_deposit(const StepDev d)
 template <class T, int NT>
 static size_t dyn_smem()
 {
-    // field tile (6 N floats) + fixed-point current tile (3 N hi + 3 N lo ints) + shared state
+    // field tile (6 N floats) + int and float current tiles (3 N each) + shared state
     return sizeof(float) * 12 * T::N + sizeof(SharedState<T, NT>);
 }
 

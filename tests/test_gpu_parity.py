@@ -60,6 +60,7 @@ def _one_step_parity(orc, wl, tol, **ctx_kw):
         for bi, (st, ids) in enumerate(states):
             st.step(1)
             errs.append(compare_box(st, ids, ctx, wl, bi, **tol))
+        print("parity errors:", errs)
         return errs
     finally:
         ctx.close()
