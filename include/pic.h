@@ -224,6 +224,34 @@ enum {
 };
 pic_status pic_info(pic_ctx* ctx, int32_t key, int64_t* out);
 
+/*
+ * pic_field_energy_noalloc -- the field energy of pic_diagnostics out[0],
+ * sum over cells of (E^2 + B^2) / 2 * cell_volume, computed in FP64 from
+ * device arrays the caller owns, without allocating any device memory.
+ * The paper has no counterpart: this is a service for callers that cannot
+ * call cudaMalloc at the moment they need the number -- code running while a
+ * stream is captured into a CUDA graph, where allocation is not allowed, and
+ * hosts that hand a library only memory they reserved in advance.
+ *   E, B         device arrays of 3 * ncells doubles each (component-major,
+ *                the layout pic_read_fields returns); read only.
+ *   ncells       number of cells, 0 <= ncells <= 44,739,242; larger sizes are
+ *                rejected with PIC_ERR_ARG (the fixed scratch holds 16,384
+ *                partial sums of 8,192 values each).
+ *   cell_volume  dx * dy * dz, > 0.
+ *   out          device pointer to one double, overwritten with the result.
+ *   stream       cudaStream_t to run on (NULL = legacy default stream); the
+ *                call returns once the work is enqueued.
+ * The partial sums live in a 128 KB array that every device loading the
+ * library holds until the process exits.  The first call on a device looks
+ * up that array's device address (cudaGetSymbolAddress), so make the first
+ * call on each device before any stream capture.  Every call overwrites the
+ * partials it reads, but calls that overlap on the GPU (other streams or
+ * host threads) share the array and race: order them on one stream.
+ * Returns PIC_ERR_ARG for bad arguments, PIC_ERR_CUDA if a launch fails.
+ */
+pic_status pic_field_energy_noalloc(const double* E, const double* B, int64_t ncells,
+                                    double cell_volume, double* out, void* stream);
+
 /* pic_last_error -- human-readable message of the last error (never NULL). */
 const char* pic_last_error(const pic_ctx* ctx);
 

@@ -32,7 +32,7 @@ FIELD_E, FIELD_B, FIELD_J, FIELD_RHO = 0, 1, 2, 3
 EXPORTED = ("pic_create", "pic_set_background", "pic_load_particles", "pic_write_fields",
             "pic_step", "pic_step_async", "pic_sync", "pic_read_fields", "pic_count_particles",
             "pic_read_particles", "pic_diagnostics", "pic_stage_timing", "pic_stage_times",
-            "pic_info", "pic_last_error", "pic_destroy")
+            "pic_info", "pic_field_energy_noalloc", "pic_last_error", "pic_destroy")
 INFO_GRAPH_ACTIVE, INFO_KERNELS_PER_STEP, INFO_POOL_FRAMES, INFO_FRAMES_USED, INFO_MOVE_CAPACITY = range(5)
 
 
@@ -93,6 +93,7 @@ def library(path: str = LIB_PATH):
     L.pic_stage_timing.argtypes = [vp, i32]
     L.pic_stage_times.argtypes = [vp, dp, ctypes.POINTER(i64)]
     L.pic_info.argtypes = [vp, i32, ctypes.POINTER(i64)]
+    L.pic_field_energy_noalloc.argtypes = [vp, vp, i64, ctypes.c_double, vp, vp]
     L.pic_last_error.argtypes = [vp]
     L.pic_last_error.restype = ctypes.c_char_p
     L.pic_destroy.argtypes = [vp]
@@ -311,6 +312,17 @@ class Context:
             self.close()
         except Exception:  # noqa: BLE001 - interpreter shutdown
             pass
+
+
+def field_energy_noalloc(E_ptr, B_ptr, ncells, cell_volume, out_ptr, stream=None):
+    """pic_field_energy_noalloc on device buffers given as raw addresses:
+    writes the FP64 field energy to *out_ptr without allocating device memory."""
+    L = library()
+    st = L.pic_field_energy_noalloc(ctypes.c_void_p(E_ptr), ctypes.c_void_p(B_ptr), int(ncells),
+                                    float(cell_volume), ctypes.c_void_p(out_ptr),
+                                    ctypes.c_void_p(stream) if stream else None)
+    if st != PIC_OK:
+        raise PicError(st, "pic_field_energy_noalloc failed")
 
 
 def from_workload(wl, precision=PRECISION_MIXED, sc=(4, 4, 4), threads_per_sc=0, track_ids=False,
