@@ -159,7 +159,7 @@ def load(ctx, X, U, Wt):
     ctx.load_particles_ptr(0, 0, n, X.data_ptr(), U.data_ptr(), Wt.data_ptr())
 
 
-def cpu_baseline_oracle(steps=5, n=32, ppc=8):
+def cpu_baseline_oracle(steps=15, n=32, ppc=8):
     """The FP64 oracle on a bounded sample of the same recipe (n^3 box)."""
     import oracle
     from paper_1606_02862_gb300 import workloads as W
@@ -380,7 +380,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=256, help="box edge in cells")
-    ap.add_argument("--sc", default="4x4x4", help="supercell edges, e.g. 8x8x4")
+    ap.add_argument("--sc", default="8x8x4", help="supercell edges, e.g. 4x4x4")
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--plain-steps", type=int, default=3)
     ap.add_argument("--no-plain", action="store_true")

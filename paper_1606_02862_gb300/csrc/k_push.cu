@@ -270,13 +270,13 @@ __device__ __forceinline__ int warp_aggregated_add(int* ctr)
     return base + __popc(mask & ((1u << lane) - 1u));
 }
 
-// Exclusive prefix sum of cnt[0..K) into off[0..K) by the whole block.
-template <int NT>
-__device__ void block_exclusive_scan_counts(const int* cnt, int* off, int K, int* s_warp)
+// Exclusive prefix sum of cnt[0..K) into off[0..K) by one warp (lanes take
+// contiguous ranges); the caller synchronises the block around it.
+__device__ __forceinline__ void warp_exclusive_scan_counts(const int* cnt, int* off, int K)
 {
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const int per = (K + NT - 1) / NT;
-    const int b0 = tid * per;
+    const int lane = threadIdx.x & 31;
+    const int per = (K + 31) / 32;
+    const int b0 = lane * per;
     int local = 0;
     for (int i = 0; i < per; ++i)
         local += (b0 + i < K) ? cnt[b0 + i] : 0;
@@ -287,22 +287,7 @@ __device__ void block_exclusive_scan_counts(const int* cnt, int* off, int K, int
         if (lane >= o)
             x += y;
     }
-    if (lane == 31)
-        s_warp[wid] = x;
-    __syncthreads();
-    if (wid == 0) {
-        int t = lane < NT / 32 ? s_warp[lane] : 0;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, t, o);
-            if (lane >= o)
-                t += y;
-        }
-        if (lane < NT / 32)
-            s_warp[lane] = t;
-    }
-    __syncthreads();
-    int run = x - local + (wid > 0 ? s_warp[wid - 1] : 0);
+    int run = x - local;
     for (int i = 0; i < per; ++i)
         if (b0 + i < K) {
             off[b0 + i] = run;
@@ -355,7 +340,6 @@ struct SharedState {
     int off[max_keys<T>()];
     int holes[kHoleCap];
     int src[kHoleCap];
-    int warp[32];
     int item, any, ngen, nholes, nhead, nsrc;
     unsigned bound_bits;  // float bits of the chunk's largest |jcoef w D|
 };
@@ -427,8 +411,9 @@ __device__ __forceinline__ void deposit_general(int* sJi, const Records<C>& r, i
 
 // ------------------------------------------------------------ one particle
 
+// Pushes one particle; returns its bound |jcoef_d w D_d| on the current terms.
 template <class T, int SHAPE, int NT>
-__device__ __forceinline__ void push_one(const StepDev& d, const SpeciesDev& sp, int s, const BoxDev& bx,
+__device__ __forceinline__ float push_one(const StepDev& d, const SpeciesDev& sp, int s, const BoxDev& bx,
                                          int scx, int scy, int scz, const float* sF,
                                          SharedState<T, NT>& sh, int j, int p, int sidx,
                                          unsigned& my_status)
@@ -495,7 +480,6 @@ __device__ __forceinline__ void push_one(const StepDev& d, const SpeciesDev& sp,
         rec.gen[atomicAdd(&sh.ngen, 1)] = sidx;
     const float bnd = fabsf(w) * fmaxf(fmaxf(fabsf(sp.jcoef[0] * Dx), fabsf(sp.jcoef[1] * Dy)),
                                        fabsf(sp.jcoef[2] * Dz));
-    atomicMax(&sh.bound_bits, __float_as_uint(bnd));
 
     // new cell and offsets
     const float fx_ = floorf(x1), fy_ = floorf(y1), fz_ = floorf(z1);
@@ -547,9 +531,24 @@ __device__ __forceinline__ void push_one(const StepDev& d, const SpeciesDev& sp,
         if (h < kHoleCap)
             sh.holes[h] = p;
     }
+    return bnd;
 }
 
 // ------------------------------------------------------------ one frame list
+
+// Add the chunk's integer tile (scaled back by inv) into the FP32 tile and
+// clear it; each thread owns its entries, no atomics.
+template <int N, int NT>
+__device__ __forceinline__ void fold_tile(int* sJi, float* sJf, float inv)
+{
+    for (int v = threadIdx.x; v < 3 * N; v += NT) {
+        const int q = sJi[v];
+        if (q != 0) {
+            sJf[v] += (float)q * inv;
+            sJi[v] = 0;
+        }
+    }
+}
 
 template <class T, int SHAPE, int NT>
 __device__ __forceinline__ void push_list(const StepDev& d, const SpeciesDev& sp, int s, int g,
@@ -564,8 +563,11 @@ __device__ __forceinline__ void push_list(const StepDev& d, const SpeciesDev& sp
     const int L = s * d.nsc + g;
     const int n = d.count[L];
     const int* ft = d.ftab + d.foff[L];
+    float prev_inv = 0.0f;
     for (int base = 0; base < n; base += C) {
         const int cn = min(C, n - base);
+        if (base > 0)
+            fold_tile<N, NT>(sJi, sJf, prev_inv);  // previous chunk, disjoint from the staging below
         for (int k = tid; k < K; k += NT)
             sh.hist[k] = 0;
         if (tid == 0) {
@@ -600,7 +602,8 @@ __device__ __forceinline__ void push_list(const StepDev& d, const SpeciesDev& sp
             sh.st.kr[j] = (key << 16) | atomicAdd(&sh.hist[key], 1);
         }
         __syncthreads();
-        block_exclusive_scan_counts<NT>(sh.hist, sh.off, K, sh.warp);
+        if (wid == 0)
+            warp_exclusive_scan_counts(sh.hist, sh.off, K);
         __syncthreads();
         for (int j = tid; j < cn; j += NT) {
             const int kr = sh.st.kr[j];
@@ -608,9 +611,17 @@ __device__ __forceinline__ void push_list(const StepDev& d, const SpeciesDev& sp
         }
         __syncthreads();
         // push in sorted order: neighbouring lanes read neighbouring field words
-        for (int sidx = tid; sidx < cn; sidx += NT) {
-            const int j = sh.st.perm[sidx];
-            push_one<T, SHAPE, NT>(d, sp, s, bx, scx, scy, scz, sF, sh, j, base + j, sidx, my_status);
+        for (int s0 = 0; s0 < cn; s0 += NT) {
+            const int sidx = s0 + tid;
+            float bnd = 0.0f;
+            if (sidx < cn) {
+                const int j = sh.st.perm[sidx];
+                bnd = push_one<T, SHAPE, NT>(d, sp, s, bx, scx, scy, scz, sF, sh, j, base + j, sidx,
+                                             my_status);
+            }
+            const unsigned m = __reduce_max_sync(0xffffffffu, __float_as_uint(bnd));
+            if (lane == 0)
+                atomicMax(&sh.bound_bits, m);
         }
         __syncthreads();
         // deposit: lanes take sorted positions C/32 apart, so one warp's
@@ -640,17 +651,11 @@ __device__ __forceinline__ void push_list(const StepDev& d, const SpeciesDev& sp
                 d.uz[idx] = sh.st.u[2][j];
             }
         }
-        __syncthreads();
-        // fold the chunk's integer tile into the FP32 tile
-        for (int v = tid; v < 3 * N; v += NT) {
-            const int q = sJi[v];
-            if (q != 0) {
-                sJf[v] += (float)q * inv;
-                sJi[v] = 0;
-            }
-        }
+        prev_inv = inv;
         __syncthreads();
     }
+    if (n > 0)
+        fold_tile<N, NT>(sJi, sJf, prev_inv);  // the caller synchronises before the flush
 }
 
 // Fill the holes the leavers left below n - nholes with the survivors above.
@@ -881,7 +886,9 @@ static cudaError_t launch_one(const StepDev& d, int grid, cudaStream_t st)
 #define PIC_PUSH_CASES(X)  \
     X(4, 4, 4, 64)         \
     X(4, 4, 4, 128)        \
+    X(4, 4, 4, 256)        \
     X(8, 4, 4, 128)        \
+    X(8, 4, 4, 256)        \
     X(8, 8, 4, 128)        \
     X(8, 8, 4, 256)        \
     X(8, 8, 8, 256)
