@@ -189,6 +189,71 @@ def cpu_model():
     return os.uname().machine
 
 
+def choose_sc(args, pic, log_fn):
+    """Supercell and threads: from --sc/--threads, or (--sc auto) the autotuner
+    run on a 64^3 sample of the same recipe, cached per GPU and build."""
+    from paper_1606_02862_gb300 import autotune
+    from paper_1606_02862_gb300 import workloads as W
+
+    if args.sc != "auto":
+        return tuple(int(v) for v in args.sc.split("x")), args.threads
+    import torch
+
+    n, ppc = 64, 8
+    X, U, Wt = make_state(torch, n, ppc, 0.05, pinned=False)
+
+    def make_ctx(sc, threads):
+        ctx = pic.Context([(n, n, n)], (1.0, 1.0, 1.0), W.DT_HALF_COURANT, [pic.Species(-1.0, 1.0, 2)],
+                          sc=sc, threads_per_sc=threads)
+        ctx.set_background(0, 0.01)
+        load(ctx, X, U, Wt)
+        return ctx
+
+    key = autotune.signature([(args.n,) * 3], ppc, [2], 1, extra="thermal_tsc")
+    sc, threads, trials = autotune.tune(make_ctx, autotune.feasible(autotune.CANDIDATES, [(n, n, n)]),
+                                        key=key, gpu_name=torch.cuda.get_device_name(), log=log_fn)
+    log_fn(f"autotune: supercell {sc}, {threads} threads ({len(trials)} timed, cached otherwise)")
+    return sc, threads
+
+
+def run_batched(args, pic, torch, sc, threads, hbm):
+    """Batched uneven boxes: 64 periodic boxes of edge 16..96 and 1..16 ppc in
+    one context (one launch per stage for all boxes) against the plain FP64
+    form (one box per launch), push+deposit rate of each."""
+    from paper_1606_02862_gb300 import workloads as W
+
+    boxes = list(W.iter_batched_uneven())
+    grids = [(b[0],) * 3 for b in boxes]
+    npart = sum(b[3].shape[0] for b in boxes)
+    ncell = sum(b[0] ** 3 for b in boxes)
+    out = {"workload": f"batched_uneven: {len(boxes)} periodic boxes, edges 16..96, ppc 1..16, "
+                       f"u_th 0.01..0.1c, TSC ({npart} particles, {ncell} cells)"}
+    for prec, steps, name in ((pic.PRECISION_MIXED, max(10, args.steps // 5), "mixed"),
+                              (pic.PRECISION_FP64_PLAIN, 2, "plain_fp64")):
+        if prec == pic.PRECISION_FP64_PLAIN and args.no_plain:
+            continue
+        ctx = pic.Context(grids, (1.0, 1.0, 1.0), W.DT_HALF_COURANT, [pic.Species(-1.0, 1.0, 2)],
+                          precision=prec, sc=sc, threads_per_sc=threads)
+        for bi, (_n, _ppc, _uth, x, u, w) in enumerate(boxes):
+            ctx.set_background(bi, 0.01)
+            ctx.load_particles(bi, 0, x, u, w)
+        ctx.step(3 if prec == pic.PRECISION_MIXED else 1)
+        ctx.stage_timing(True)
+        ctx.step(steps)
+        ms, nst = ctx.stage_times()
+        ctx.close()
+        pd = (ms[0] + ms[1]) / nst
+        per_p = MIXED_BYTES_PER_PARTICLE if prec == pic.PRECISION_MIXED else PLAIN_BYTES_PER_PARTICLE
+        per_c = MIXED_BYTES_PER_CELL if prec == pic.PRECISION_MIXED else PLAIN_BYTES_PER_CELL
+        out[name] = {"value": npart / (pd * 1e-3), "unit": UNIT, "push_deposit_ms": pd,
+                     "step_ms": ms[3] / nst, "steps": nst,
+                     "hbm_frac": (npart * per_p + ncell * per_c) / (ms[0] / nst * 1e-3) / 1e9 / hbm}
+        log(f"batched {name}: push+deposit {pd:.3f} ms, step {ms[3] / nst:.3f} ms")
+    if "plain_fp64" in out:
+        out["mixed_over_plain"] = out["mixed"]["value"] / out["plain_fp64"]["value"]
+    return out
+
+
 def run_ours(args, rank, world, dist):
     import torch
 
@@ -207,7 +272,9 @@ def run_ours(args, rank, world, dist):
     torch.cuda.set_stream(stream)
 
     n, ppc, u_th = args.n, 8, 0.05
-    sc = tuple(int(v) for v in args.sc.split("x"))
+    sc, threads = choose_sc(args, pic, log)
+    args.threads = threads
+    args.sc = "x".join(str(v) for v in sc)
     ncell = n ** 3
     t0 = time.perf_counter()
     X, U, Wt = make_state(torch, n, ppc, u_th)
@@ -306,6 +373,11 @@ def run_ours(args, rank, world, dist):
                            "bytes_per_particle": PLAIN_BYTES_PER_PARTICLE}
         log(f"[rank {rank}] plain fp64: push {p_ms:.2f} ms")
 
+    # ---------------- batched uneven boxes, mixed vs plain
+    if not args.no_batched and rank == 0:
+        del X, U, Wt
+        result["batched"] = run_batched(args, pic, torch, sc, threads, hbm)
+
     if rank != 0:
         return None
     line = {
@@ -336,6 +408,8 @@ def run_ours(args, rank, world, dist):
         line["plain_fp64"] = result["plain"]
     if "e2e" in result:
         line["e2e"] = result["e2e"]
+    if "batched" in result:
+        line["batched"] = result["batched"]
     if world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline_oracle()
     return line
@@ -380,12 +454,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=256, help="box edge in cells")
-    ap.add_argument("--sc", default="8x8x4", help="supercell edges, e.g. 4x4x4")
+    ap.add_argument("--sc", default="auto", help="supercell edges, e.g. 8x8x4, or auto")
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--plain-steps", type=int, default=3)
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 

@@ -215,13 +215,11 @@ def laser_ramp(nx=128, ny=1024, nz=128, ppc=4, seed_offset=2, lam=32.0, a0=3.0, 
     return Workload("laser_ramp", DT_HALF_COURANT, sp, [box], steps=1000)
 
 
-def batched_uneven(nboxes=64, seed_offset=3, sizes=tuple(range(16, 97, 8)), max_ppc=16) -> Workload:
-    """nboxes independent periodic cubic boxes; edge drawn uniformly from
-    sizes, ppc from 1..max_ppc, u_th from U[0.01, 0.1]; electrons, TSC,
-    density 0.01 plus background."""
+def iter_batched_uneven(nboxes=64, seed_offset=3, sizes=tuple(range(16, 97, 8)), max_ppc=16,
+                        dens=0.01):
+    """Yield the boxes of batched_uneven one at a time: (n, ppc, u_th, x, u, w),
+    from one PCG64 stream, so a caller never holds more than one box."""
     rng = np.random.default_rng(BASE_SEED + seed_offset)
-    boxes = []
-    dens = 0.01
     for _ in range(nboxes):
         n = int(rng.choice(sizes))
         ppc = int(rng.integers(1, max_ppc + 1))
@@ -229,7 +227,16 @@ def batched_uneven(nboxes=64, seed_offset=3, sizes=tuple(range(16, 97, 8)), max_
         x = uniform_in_cells(rng, n, n, n, ppc)
         u = maxwellian(rng, x.shape[0], u_th)
         w = np.full(x.shape[0], dens / ppc)
-        boxes.append(BoxInit(n, n, n, particles=[(x, u, w)], rho_bg=dens))
+        yield n, ppc, u_th, x, u, w
+
+
+def batched_uneven(nboxes=64, seed_offset=3, sizes=tuple(range(16, 97, 8)), max_ppc=16) -> Workload:
+    """nboxes independent periodic cubic boxes; edge drawn uniformly from
+    sizes, ppc from 1..max_ppc, u_th from U[0.01, 0.1]; electrons, TSC,
+    density 0.01 plus background."""
+    dens = 0.01
+    boxes = [BoxInit(n, n, n, particles=[(x, u, w)], rho_bg=dens)
+             for n, _ppc, _uth, x, u, w in iter_batched_uneven(nboxes, seed_offset, sizes, max_ppc, dens)]
     return Workload("batched_uneven", DT_HALF_COURANT, [SpeciesDef("e", -1.0, 1.0, 2)], boxes,
                     steps=500)
 
