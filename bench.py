@@ -216,16 +216,25 @@ def choose_sc(args, pic, log_fn):
     return sc, threads
 
 
-def run_batched(args, pic, torch, sc, threads, hbm):
+def run_batched(args, pic, torch, sc, threads, hbm, rank=0, world=1, dist=None):
     """Batched uneven boxes: 64 periodic boxes of edge 16..96 and 1..16 ppc in
     one context (one launch per stage for all boxes) against the plain FP64
-    form (one box per launch), push+deposit rate of each."""
+    form (one box per launch), push+deposit rate of each.  With several ranks
+    the boxes are partitioned over them (no data exchange) and the rate is
+    all particles / slowest rank."""
+    from paper_1606_02862_gb300 import shard
     from paper_1606_02862_gb300 import workloads as W
 
-    boxes = list(W.iter_batched_uneven())
+    allb = list(W.iter_batched_uneven())
+    costs = [shard.box_cost(b[0] ** 3, b[3].shape[0]) for b in allb]
+    mine = shard.partition(costs, world)[rank]
+    boxes = [allb[i] for i in mine]
+    del allb
     grids = [(b[0],) * 3 for b in boxes]
-    npart = sum(b[3].shape[0] for b in boxes)
-    ncell = sum(b[0] ** 3 for b in boxes)
+    npart_mine = sum(b[3].shape[0] for b in boxes)
+    npart, ncell = shard.sum_over_ranks([npart_mine, sum(b[0] ** 3 for b in boxes)], dist,
+                                        device="cuda")
+    npart, ncell = int(npart), int(ncell)
     out = {"workload": f"batched_uneven: {len(boxes)} periodic boxes, edges 16..96, ppc 1..16, "
                        f"u_th 0.01..0.1c, TSC ({npart} particles, {ncell} cells)"}
     for prec, steps, name in ((pic.PRECISION_MIXED, max(10, args.steps // 5), "mixed"),
@@ -242,13 +251,14 @@ def run_batched(args, pic, torch, sc, threads, hbm):
         ctx.step(steps)
         ms, nst = ctx.stage_times()
         ctx.close()
-        pd = (ms[0] + ms[1]) / nst
+        pd, push_ms, step_ms = shard.max_over_ranks([(ms[0] + ms[1]) / nst, ms[0] / nst, ms[3] / nst],
+                                                    dist, device="cuda")
         per_p = MIXED_BYTES_PER_PARTICLE if prec == pic.PRECISION_MIXED else PLAIN_BYTES_PER_PARTICLE
         per_c = MIXED_BYTES_PER_CELL if prec == pic.PRECISION_MIXED else PLAIN_BYTES_PER_CELL
         out[name] = {"value": npart / (pd * 1e-3), "unit": UNIT, "push_deposit_ms": pd,
-                     "step_ms": ms[3] / nst, "steps": nst,
-                     "hbm_frac": (npart * per_p + ncell * per_c) / (ms[0] / nst * 1e-3) / 1e9 / hbm}
-        log(f"batched {name}: push+deposit {pd:.3f} ms, step {ms[3] / nst:.3f} ms")
+                     "step_ms": step_ms, "steps": nst,
+                     "hbm_frac": (npart * per_p + ncell * per_c) / world / (push_ms * 1e-3) / 1e9 / hbm}
+        log(f"[rank {rank}] batched {name}: push+deposit {pd:.3f} ms, step {step_ms:.3f} ms")
     if "plain_fp64" in out:
         out["mixed_over_plain"] = out["mixed"]["value"] / out["plain_fp64"]["value"]
     return out
@@ -258,7 +268,7 @@ def run_ours(args, rank, world, dist):
     import torch
 
     from paper_1606_02862_gb300 import build as libbuild
-    from paper_1606_02862_gb300 import pic
+    from paper_1606_02862_gb300 import pic, shard
 
     if not torch.cuda.is_available():
         raise SystemExit("bench.py needs a CUDA GPU")
@@ -315,12 +325,7 @@ def run_ours(args, rank, world, dist):
     yee_ms = stage_ms[2] / args.steps
     step_ms = total_ms / args.steps
     pd_ms = push_ms + frames_ms
-    times = torch.tensor([pd_ms, step_ms], dtype=torch.float64)
-    if dist is not None:
-        t = times.cuda()
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        times = t.cpu()
-    pd_ms_max, step_ms_max = float(times[0]), float(times[1])
+    pd_ms_max, step_ms_max = shard.max_over_ranks([pd_ms, step_ms], dist, device="cuda")
     value = world * npart / (pd_ms_max * 1e-3)
     push_bytes = npart * MIXED_BYTES_PER_PARTICLE + ncell * MIXED_BYTES_PER_CELL
     achieved = push_bytes / (push_ms * 1e-3) / 1e9
@@ -374,9 +379,12 @@ def run_ours(args, rank, world, dist):
         log(f"[rank {rank}] plain fp64: push {p_ms:.2f} ms")
 
     # ---------------- batched uneven boxes, mixed vs plain
-    if not args.no_batched and rank == 0:
+    if not args.no_batched:
         del X, U, Wt
-        result["batched"] = run_batched(args, pic, torch, sc, threads, hbm)
+        result["batched"] = run_batched(args, pic, torch, sc, threads, hbm, rank, world, dist)
+        if world > 1:
+            result["batched"]["parallelism"] = f"boxes partitioned over {world} ranks"
+            result["batched"]["scaling"] = "strong"
 
     if rank != 0:
         return None
