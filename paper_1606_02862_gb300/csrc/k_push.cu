@@ -310,13 +310,18 @@ struct Stage {
     int perm[C];  // sorted position -> chunk position
 };
 
-// Deposit inputs of the chunk's moves, by sorted position.
+// Deposit inputs of the chunk's moves, by sorted position s stored at slot
+// rslot(s) = s + s / 32: the deposit reads them with a stride of C / 32
+// between lanes, and the skew puts the 32 lanes on 32 different banks.
+__host__ __device__ constexpr int rslot(int s) { return s + (s >> 5); }
+
 template <int C>
 struct Records {
-    int l[C];        // packed local cell lx | ly << 8 | lz << 16, bit 24: general window
-    float o[3][C];   // old in-cell offsets
-    float D[3][C];   // displacement in cells
-    float w[C];      // weight
+    static constexpr int R = C + C / 32;
+    int l[R];        // packed local cell lx | ly << 8 | lz << 16, bit 24: general window
+    float o[3][R];   // old in-cell offsets
+    float D[3][R];   // displacement in cells
+    float w[R];      // weight
     int gen[C];      // sorted positions of the moves that need the general window
 };
 
@@ -349,9 +354,10 @@ struct SharedState {
 // Common window: nodes a-1, a, a+1 (TSC, a = round(o)) or 0, 1 (CIC) on every
 // axis; S0 is the particle's shape there and DS has closed forms in D.
 template <class T, int SHAPE, int C>
-__device__ __forceinline__ void deposit_common(int* sJi, const Records<C>& r, int e, const float jc[3],
+__device__ __forceinline__ void deposit_common(int* sJi, const Records<C>& r, int s, const float jc[3],
                                                float scale)
 {
+    const int e = rslot(s);
     constexpr int NW = SHAPE == 2 ? 3 : 2;
     const int l = r.l[e];
     const int lc[3] = {l & 0xff, (l >> 8) & 0xff, (l >> 16) & 0xff};
@@ -388,9 +394,10 @@ __device__ __forceinline__ void deposit_common(int* sJi, const Records<C>& r, in
 
 // General window: nodes l-1 .. l+2 on every axis.
 template <class T, int SHAPE, int C>
-__device__ __forceinline__ void deposit_general(int* sJi, const Records<C>& r, int e, const float jc[3],
+__device__ __forceinline__ void deposit_general(int* sJi, const Records<C>& r, int s, const float jc[3],
                                                 float scale)
 {
+    const int e = rslot(s);
     const int l = r.l[e];
     float S0[3][4], DS[3][4];
 #pragma unroll
@@ -468,14 +475,15 @@ __device__ __forceinline__ float push_one(const StepDev& d, const SpeciesDev& sp
                  ((oz >= 0.5f) == (z1 >= 0.5f));
     else
         common = x1 >= 0.0f && x1 < 1.0f && y1 >= 0.0f && y1 < 1.0f && z1 >= 0.0f && z1 < 1.0f;
-    rec.l[sidx] = lx | (ly << 8) | (lz << 16) | (common ? 0 : (1 << 24));
-    rec.o[0][sidx] = ox;
-    rec.o[1][sidx] = oy;
-    rec.o[2][sidx] = oz;
-    rec.D[0][sidx] = Dx;
-    rec.D[1][sidx] = Dy;
-    rec.D[2][sidx] = Dz;
-    rec.w[sidx] = w;
+    const int rs = rslot(sidx);
+    rec.l[rs] = lx | (ly << 8) | (lz << 16) | (common ? 0 : (1 << 24));
+    rec.o[0][rs] = ox;
+    rec.o[1][rs] = oy;
+    rec.o[2][rs] = oz;
+    rec.D[0][rs] = Dx;
+    rec.D[1][rs] = Dy;
+    rec.D[2][rs] = Dz;
+    rec.w[rs] = w;
     if (!common)
         rec.gen[atomicAdd(&sh.ngen, 1)] = sidx;
     const float bnd = fabsf(w) * fmaxf(fmaxf(fabsf(sp.jcoef[0] * Dx), fabsf(sp.jcoef[1] * Dy)),
@@ -630,11 +638,11 @@ __device__ __forceinline__ void push_list(const StepDev& d, const SpeciesDev& sp
         const float scale = chunk_scale(cn, __uint_as_float(sh.bound_bits), &inv);
         for (int r = 0; r < C / NT; ++r) {
             const int e = lane * (C / 32) + wid * (C / NT) + r;
-            if (e < cn && !(sh.rec.l[e] >> 24))
+            if (e < cn && !(sh.rec.l[rslot(e)] >> 24))
                 deposit_common<T, SHAPE, C>(sJi, sh.rec, e, sp.jcoef, scale);
         }
         const int ngen = sh.ngen;
-        for (int q = tid; q < ngen; q += NT)
+        for (int q = tid; q < ngen; q += NT)  // packed into as few warps as possible
             deposit_general<T, SHAPE, C>(sJi, sh.rec, sh.rec.gen[q], sp.jcoef, scale);
         // write the chunk back (coalesced)
         for (int j = tid; j < cn; j += NT) {
@@ -783,6 +791,7 @@ __global__ void __launch_bounds__(NT, 768 / NT) k_push_deposit(const StepDev d)
             __syncthreads();  // item / any are rewritten next round
             continue;
         }
+
 
         // ---- 1. stage the E/B tile, zero the J tiles
         const int64_t pcell = padded_cells(bx);
