@@ -47,7 +47,7 @@
 
 namespace pic {
 
-constexpr int kHoleCap = 512;
+constexpr int kHoleCap = 256;
 
 template <int LX_, int LY_, int LZ_>
 struct Tile {
@@ -749,7 +749,7 @@ __device__ __forceinline__ void compact_list(const StepDev& d, int L, int n, int
 // ------------------------------------------------------------ the kernel
 
 template <class T, int NT>
-__global__ void __launch_bounds__(NT, 768 / NT) k_push_deposit(const StepDev d)
+__global__ void __launch_bounds__(NT, 1024 / NT) k_push_deposit(const StepDev d)
 {
     constexpr int TX = T::TX, TY = T::TY, TZ = T::TZ, PX = T::PX, N = T::N;
     constexpr int LX = T::LX, LY = T::LY, LZ = T::LZ;
