@@ -423,6 +423,58 @@ def run_ours(args, rank, world, dist):
     return line
 
 
+# ----------------------------------------------------------------------------- other workloads
+
+WORKLOADS = {
+    "small_cic_32": "32^3 periodic, electrons 2 ppc, u_th 0.01c, B_z 0.1, CIC",
+    "laser_ramp": "128x1024x128, e- + p+ 4 ppc each in a density ramp to 0.01 n_c, Gaussian pulse a0 3",
+    "foil_overdense": "256x2048x256, 20-cell foil of e- + C6+ at 30 n_c, 16 ppc each, Gaussian pulse a0 10",
+}
+
+
+def run_workload(args):
+    """Push+deposit rate of one of the other synthetic workloads (mixed form,
+    graph replay, in-graph stage events), as its own JSON line."""
+    import torch
+
+    from paper_1606_02862_gb300 import build as libbuild
+    from paper_1606_02862_gb300 import pic
+    from paper_1606_02862_gb300 import workloads as W
+
+    libbuild.build()
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    t0 = time.perf_counter()
+    wl = getattr(W, args.workload)()
+    log(f"generated {args.workload} in {time.perf_counter() - t0:.1f} s")
+    sc = (8, 4, 4) if args.sc == "auto" else tuple(int(v) for v in args.sc.split("x"))
+    threads = args.threads or 256
+    ctx = pic.from_workload(wl, sc=sc, threads_per_sc=threads)
+    npart = sum(ctx.count_particles(b, s) for b in range(len(wl.boxes)) for s in range(len(wl.species))
+                if wl.species[s].mobile)
+    ncell = wl.ncells
+    del wl
+    ctx.step(args.warmup)
+    ctx.stage_timing(True)
+    ctx.step(args.steps)
+    ms, nst = ctx.stage_times()
+    ctx.close()
+    pd = (ms[0] + ms[1]) / nst
+    hbm, hbm_src = measured_hbm()
+    achieved = (npart * MIXED_BYTES_PER_PARTICLE + ncell * MIXED_BYTES_PER_CELL) / (ms[0] / nst * 1e-3) / 1e9
+    return {"metric": METRIC, "value": npart / (pd * 1e-3), "unit": UNIT, "n_gpus": 1,
+            "steps": nst, "warmup": args.warmup, "ms_per_step": ms[3] / nst, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]} ({npart} particles, "
+                                   f"{ncell} cells)",
+                       "form": f"mixed, supercell {'x'.join(map(str, sc))}, {threads} threads"},
+            "stage_ms_per_step": {"push_deposit_kernel": ms[0] / nst, "frame_maintenance": ms[1] / nst,
+                                  "yee": ms[2] / nst},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm, "traffic": None, "kernel": "k_push_deposit",
+                         "peak_source": hbm_src}}
+
+
 # ----------------------------------------------------------------------------- reference arm
 
 def run_reference(args, rank):
@@ -469,6 +521,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--workload", default="thermal_tsc_256",
+                    choices=["thermal_tsc_256", "small_cic_32", "laser_ramp", "foil_overdense"])
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -482,6 +536,8 @@ def main():
         dist = dist_mod
     if args.impl == "reference":
         line = run_reference(args, rank)
+    elif args.workload != "thermal_tsc_256":
+        line = run_workload(args) if rank == 0 else None
     else:
         line = run_ours(args, rank, world, dist)
     if rank == 0 and line is not None:

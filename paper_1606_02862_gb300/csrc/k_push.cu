@@ -63,37 +63,74 @@ struct Tile {
 // ------------------------------------------------------------ shape factors
 
 // TSC (quadratic spline, Hockney & Eastwood) at distance d, branch-free.
-__device__ __forceinline__ float tsc_S(float d)
+__host__ __device__ __forceinline__ float tsc_S(float d)
 {
     float a = fabsf(d);
     float t = fmaxf(1.5f - a, 0.0f);
     return a <= 0.5f ? 0.75f - a * a : 0.5f * t * t;
 }
 
-// S(d0 + D) - S(d0) for TSC; when both ends lie on one spline piece the
-// difference is factored through D so it keeps FP32 relative accuracy.
-__device__ __forceinline__ float tsc_dS(float d0, float D)
+// S(d0 + D) - S(d0) for TSC without ever forming d1 = d0 + D (rounding d1
+// costs ~6e-8 absolute, which is a large relative error on a DS of order D
+// for slow particles).  On one spline piece the difference is factored
+// through D; across a piece boundary p (|d| = 1/2 or 3/2) it is the sum of
+// the two pieces' differences to p, with the exact distance d0 -> p
+// (Sterbenz) and the remainder D - (p - d0).  The spline is C1 at its joins,
+// so a misjudged side of p changes the result only at second order.
+__host__ __device__ __forceinline__ float tsc_dS(float d0, float D)
 {
-    float d1 = d0 + D;
-    float a0 = fabsf(d0), a1 = fabsf(d1);
-    int p0 = a0 <= 0.5f ? 0 : (a0 < 1.5f ? 1 : 2);
-    int p1 = a1 <= 0.5f ? 0 : (a1 < 1.5f ? 1 : 2);
-    float s = d0 >= 0.0f ? 1.0f : -1.0f;  // |D| < 1/2: both outer ends share the sign
-    float centre = -D * (d0 + d1);
-    float outer = -0.5f * s * D * (3.0f - s * (d0 + d1));
-    float general = tsc_S(d1) - tsc_S(d0);
-    float same = p0 == 0 ? centre : (p0 == 1 ? outer : 0.0f);
-    return p0 == p1 ? same : general;
+    const float a0 = fabsf(d0);
+    const float s0 = d0 >= 0.0f ? 1.0f : -1.0f;
+    if (a0 <= 0.5f) {
+        const float d1 = d0 + D;  // classification only
+        if (fabsf(d1) <= 0.5f)
+            return -D * (2.0f * d0 + D);                 // centre piece: d0^2 - d1^2
+        const float p = d1 >= 0.0f ? 0.5f : -0.5f;
+        const float u1 = p - d0;                          // exact distance to the join
+        const float t = (d1 >= 0.0f ? 1.0f : -1.0f) * (D - u1);  // |d1| - 1/2 >= 0
+        return -u1 * (p + d0) + t * (0.5f * t - 1.0f);   // centre to p, then outer piece
+    }
+    const float a1 = a0 + s0 * D;  // |d1| on this side (classification)
+    if (a0 < 1.5f) {
+        if (a1 <= 0.5f) {                                 // outer piece into the centre
+            const float p = 0.5f * s0;
+            const float t0 = a0 - 0.5f;                   // exact
+            const float u2 = s0 * t0 + D;                 // d1 - p
+            return t0 * (1.0f - 0.5f * t0) - u2 * (2.0f * p + u2);
+        }
+        if (a1 < 1.5f)                                    // outer piece
+            return -0.5f * s0 * D * (3.0f - 2.0f * a0 - s0 * D);
+        const float r0 = 1.5f - a0;                       // out of the support
+        return -0.5f * r0 * r0;
+    }
+    if (a1 < 1.5f) {                                      // into the support
+        const float r1 = (1.5f - a0) - s0 * D;            // 1.5 - |d1|
+        return 0.5f * r1 * r1;
+    }
+    return 0.0f;
 }
 
-__device__ __forceinline__ float cic_S(float d) { return fmaxf(0.0f, 1.0f - fabsf(d)); }
+__host__ __device__ __forceinline__ float cic_S(float d) { return fmaxf(0.0f, 1.0f - fabsf(d)); }
 
-__device__ __forceinline__ float cic_dS(float d0, float D)
+// S(d0 + D) - S(d0) for CIC, the same way: across the node (d = 0) the
+// difference is s0 (2 d0 + D); across the support edge (|d| = 1, a kink, so
+// the side is decided exactly: 1 - |d0| is exact and compared with s0 D)
+// it is the distance to the edge.
+__host__ __device__ __forceinline__ float cic_dS(float d0, float D)
 {
-    float d1 = d0 + D;
-    bool same = fabsf(d0) < 1.0f && fabsf(d1) < 1.0f && ((d0 >= 0.0f) == (d1 >= 0.0f));
-    float f = d0 >= 0.0f ? -D : D;
-    return same ? f : cic_S(d1) - cic_S(d0);
+    const float a0 = fabsf(d0);
+    const float s0 = d0 >= 0.0f ? 1.0f : -1.0f;
+    if (a0 < 1.0f) {
+        if (a0 >= 0.5f && s0 * D >= 1.0f - a0)
+            return -(1.0f - a0);                          // out of the support
+        const float d1 = d0 + D;                          // its sign is exact
+        if ((d1 >= 0.0f) == (d0 >= 0.0f))
+            return -s0 * D;
+        return s0 * (2.0f * d0 + D);                      // across the node
+    }
+    if (-s0 * D > a0 - 1.0f)
+        return (1.0f - a0) - s0 * D;                      // into the support: 1 - |d1|
+    return 0.0f;
 }
 
 // Gather weights along one axis for a particle at offset o in [0,1) of its
@@ -169,8 +206,8 @@ __device__ __forceinline__ float esk_T(float s0e, float dse, float s0f, float ds
 // memory int32 atomics are native, where FP32 shared atomics are a
 // compare-and-swap loop.  A chunk's contributions are scaled by a power of
 // two chosen from the chunk itself: with B = max over its particles and
-// axes of |jcoef_d w D_d| (|P| <= |D| and |T| <= 1 bound every term of the
-// current by it) and n <= 256 particles, each scaled term is below 2^21 and a
+// axes of Tmax |jcoef_d w D_d| (|P| <= |D| and |T| <= Tmax = (max S)^2 bound
+// every term of the current by it) and n <= 256 particles, each scaled term is below 2^21 and a
 // node's sum below 2^30, so nothing overflows and a term keeps 2^-22 B
 // resolution.
 // After the chunk the integer tile is folded into an FP32 tile.  Scaled terms
@@ -486,8 +523,12 @@ __device__ __forceinline__ float push_one(const StepDev& d, const SpeciesDev& sp
     rec.w[rs] = w;
     if (!common)
         rec.gen[atomicAdd(&sh.ngen, 1)] = sidx;
-    const float bnd = fabsf(w) * fmaxf(fmaxf(fabsf(sp.jcoef[0] * Dx), fabsf(sp.jcoef[1] * Dy)),
-                                       fabsf(sp.jcoef[2] * Dz));
+    // bound on every current term of this particle: |jcoef_d w P| with |P| <= |D_d|
+    // (P is a difference of cumulative shape sums, whose slope is at most 1),
+    // times |T| <= (max S)^2: 9/16 for TSC (S <= 3/4), 1 for CIC
+    const float tmax = SHAPE == 2 ? 0.5625f * 1.001f : 1.0f;
+    const float bnd = tmax * fabsf(w) * fmaxf(fmaxf(fabsf(sp.jcoef[0] * Dx), fabsf(sp.jcoef[1] * Dy)),
+                                              fabsf(sp.jcoef[2] * Dz));
 
     // new cell and offsets
     const float fx_ = floorf(x1), fy_ = floorf(y1), fz_ = floorf(z1);

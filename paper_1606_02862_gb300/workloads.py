@@ -242,10 +242,11 @@ def batched_uneven(nboxes=64, seed_offset=3, sizes=tuple(range(16, 97, 8)), max_
 
 
 def foil_overdense(nx=256, ny=2048, nz=256, ppc=16, seed_offset=4, lam=32.0, a0=10.0,
-                   waist=16.0, duration=40.0, foil=(512, 532), n_e_over_nc=30.0) -> Workload:
+                   waist=16.0, duration=40.0, foil=(512, 532), n_e_over_nc=30.0,
+                   pulse_gap=100.0) -> Workload:
     """A foil y in [foil[0], foil[1]) of electrons at n_e_over_nc n_c and C6+
     at a sixth of that (neutral), ppc each, in vacuum; Gaussian pulse centred
-    100 cells before the foil."""
+    pulse_gap cells before the foil."""
     rng = np.random.default_rng(BASE_SEED + seed_offset)
     nc = (2.0 * math.pi / lam) ** 2
     ne = n_e_over_nc * nc
@@ -253,7 +254,7 @@ def foil_overdense(nx=256, ny=2048, nz=256, ppc=16, seed_offset=4, lam=32.0, a0=
     xi = uniform_in_cells(rng, nx, ny, nz, ppc, y_lo=foil[0], y_hi=foil[1])
     ue = maxwellian(rng, xe.shape[0], 0.001)
     ui = maxwellian(rng, xi.shape[0], 0.001 / math.sqrt(C6_MASS))
-    E, B = gaussian_pulse_y(nx, ny, nz, a0, lam, waist, duration, foil[0] - 100.0)
+    E, B = gaussian_pulse_y(nx, ny, nz, a0, lam, waist, duration, foil[0] - pulse_gap)
     box = BoxInit(nx, ny, nz, particles=[(xe, ue, np.full(xe.shape[0], ne / ppc)),
                                          (xi, ui, np.full(xi.shape[0], ne / 6.0 / ppc))], E=E, B=B)
     sp = [SpeciesDef("e", -1.0, 1.0, 2), SpeciesDef("C6+", 6.0, C6_MASS, 2)]
