@@ -144,11 +144,14 @@ def make_state(torch, n, ppc, u_th, pinned=True):
     return X, U, Wt
 
 
-def new_ctx(pic, n, precision, sc, threads):
+SHAPE = {"tsc": 2, "cic": 1}
+
+
+def new_ctx(pic, n, precision, sc, threads, shape=2):
     from paper_1606_02862_gb300 import workloads as W
 
     ctx = pic.Context([(n, n, n)], (1.0, 1.0, 1.0), W.DT_HALF_COURANT,
-                      [pic.Species(-1.0, 1.0, 2, True)], precision=precision, sc=sc,
+                      [pic.Species(-1.0, 1.0, shape, True)], precision=precision, sc=sc,
                       threads_per_sc=threads, use_graph=True)
     ctx.set_background(0, 0.01)
     return ctx
@@ -203,13 +206,13 @@ def choose_sc(args, pic, log_fn):
     X, U, Wt = make_state(torch, n, ppc, 0.05, pinned=False)
 
     def make_ctx(sc, threads):
-        ctx = pic.Context([(n, n, n)], (1.0, 1.0, 1.0), W.DT_HALF_COURANT, [pic.Species(-1.0, 1.0, 2)],
-                          sc=sc, threads_per_sc=threads)
+        ctx = pic.Context([(n, n, n)], (1.0, 1.0, 1.0), W.DT_HALF_COURANT,
+                          [pic.Species(-1.0, 1.0, SHAPE[args.shape])], sc=sc, threads_per_sc=threads)
         ctx.set_background(0, 0.01)
         load(ctx, X, U, Wt)
         return ctx
 
-    key = autotune.signature([(args.n,) * 3], ppc, [2], 1, extra="thermal_tsc")
+    key = autotune.signature([(args.n,) * 3], ppc, [SHAPE[args.shape]], 1, extra="thermal")
     sc, threads, trials = autotune.tune(make_ctx, autotune.feasible(autotune.CANDIDATES, [(n, n, n)]),
                                         key=key, gpu_name=torch.cuda.get_device_name(), log=log_fn)
     log_fn(f"autotune: supercell {sc}, {threads} threads ({len(trials)} timed, cached otherwise)")
@@ -295,7 +298,7 @@ def run_ours(args, rank, world, dist):
     result = {}
 
     # ---------------- mixed form, device-resident inputs, graph replay
-    ctx = new_ctx(pic, n, pic.PRECISION_MIXED, sc, args.threads)
+    ctx = new_ctx(pic, n, pic.PRECISION_MIXED, sc, args.threads, SHAPE[args.shape])
     t0 = time.perf_counter()
     load(ctx, X, U, Wt)
     log(f"[rank {rank}] loaded in {time.perf_counter() - t0:.1f} s")
@@ -344,7 +347,7 @@ def run_ours(args, rank, world, dist):
         Eo = np.empty((3, n, n, n))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        ctx = new_ctx(pic, n, pic.PRECISION_MIXED, sc, args.threads)
+        ctx = new_ctx(pic, n, pic.PRECISION_MIXED, sc, args.threads, SHAPE[args.shape])
         load(ctx, X, U, Wt)
         ctx.step(args.steps)
         nout = ctx.read_particles_ptr(0, 0, npart, Xo.data_ptr(), Uo.data_ptr(), Wo.data_ptr())
@@ -363,7 +366,7 @@ def run_ours(args, rank, world, dist):
 
     # ---------------- plain FP64 GPU form, same workload
     if not args.no_plain:
-        ctx = new_ctx(pic, n, pic.PRECISION_FP64_PLAIN, sc, 0)
+        ctx = new_ctx(pic, n, pic.PRECISION_FP64_PLAIN, sc, 0, SHAPE[args.shape])
         load(ctx, X, U, Wt)
         ctx.step(1)
         ctx.stage_timing(True)
@@ -393,9 +396,9 @@ def run_ours(args, rank, world, dist):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": result["step_ms"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": f"thermal_tsc_{n}: {n}^3 periodic cells, electrons {ppc} ppc "
-                               f"({npart} particles/GPU), u_th 0.05c, TSC, dt = 0.5 Courant, "
-                               "neutralising background",
+        "config": {"workload": f"thermal_{args.shape}_{n}: {n}^3 periodic cells, electrons {ppc} ppc "
+                               f"({npart} particles/GPU), u_th 0.05c, {args.shape.upper()}, "
+                               "dt = 0.5 Courant, neutralising background",
                    "form": f"mixed: int32 cell + FP32 offsets, supercell frames {args.sc}, "
                            f"{args.threads or 'default'} threads/supercell",
                    "graph": result["graph"],
@@ -429,6 +432,7 @@ WORKLOADS = {
     "small_cic_32": "32^3 periodic, electrons 2 ppc, u_th 0.01c, B_z 0.1, CIC",
     "laser_ramp": "128x1024x128, e- + p+ 4 ppc each in a density ramp to 0.01 n_c, Gaussian pulse a0 3",
     "foil_overdense": "256x2048x256, 20-cell foil of e- + C6+ at 30 n_c, 16 ppc each, Gaussian pulse a0 10",
+    "khi_128": "128^3, e- + p+ 16 ppc each, shear slabs at +-0.2c, TSC (the paper's evaluation size)",
 }
 
 
@@ -445,7 +449,7 @@ def run_workload(args):
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     t0 = time.perf_counter()
-    wl = getattr(W, args.workload)()
+    wl = W.khi() if args.workload == "khi_128" else getattr(W, args.workload)()
     log(f"generated {args.workload} in {time.perf_counter() - t0:.1f} s")
     sc = (8, 4, 4) if args.sc == "auto" else tuple(int(v) for v in args.sc.split("x"))
     threads = args.threads or 256
@@ -453,12 +457,23 @@ def run_workload(args):
     npart = sum(ctx.count_particles(b, s) for b in range(len(wl.boxes)) for s in range(len(wl.species))
                 if wl.species[s].mobile)
     ncell = wl.ncells
-    del wl
     ctx.step(args.warmup)
     ctx.stage_timing(True)
     ctx.step(args.steps)
     ms, nst = ctx.stage_times()
     ctx.close()
+    plain = None
+    if args.workload == "khi_128" and not args.no_plain:
+        # the paper runs this workload in single and double precision
+        pctx = pic.from_workload(wl, precision=pic.PRECISION_FP64_PLAIN)
+        pctx.step(1)
+        pctx.stage_timing(True)
+        pctx.step(args.plain_steps)
+        pms, pn = pctx.stage_times()
+        pctx.close()
+        plain = {"value": npart / (pms[0] / pn * 1e-3), "unit": UNIT, "push_ms": pms[0] / pn,
+                 "step_ms": pms[3] / pn, "steps": pn}
+    del wl
     pd = (ms[0] + ms[1]) / nst
     hbm, hbm_src = measured_hbm()
     achieved = (npart * MIXED_BYTES_PER_PARTICLE + ncell * MIXED_BYTES_PER_CELL) / (ms[0] / nst * 1e-3) / 1e9
@@ -472,7 +487,9 @@ def run_workload(args):
                                   "yee": ms[2] / nst},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "traffic": None, "kernel": "k_push_deposit",
-                         "peak_source": hbm_src}}
+                         "peak_source": hbm_src},
+            **({"plain_fp64": plain, "fp32_over_fp64": plain["step_ms"] and (plain["step_ms"] / (ms[3] / nst))}
+               if plain else {})}
 
 
 # ----------------------------------------------------------------------------- reference arm
@@ -521,8 +538,11 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--shape", default="tsc", choices=["tsc", "cic"],
+                    help="particle shape of the headline thermal workload")
     ap.add_argument("--workload", default="thermal_tsc_256",
-                    choices=["thermal_tsc_256", "small_cic_32", "laser_ramp", "foil_overdense"])
+                    choices=["thermal_tsc_256", "small_cic_32", "laser_ramp", "foil_overdense",
+                             "khi_128"])
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 

@@ -1,7 +1,8 @@
-"""The laser-plasma workloads (electron + ion species, a Gaussian pulse
-along y, a density ramp or an overdense foil, most supercells empty) at
-reduced size: one-step parity with the FP64 oracle, and invariants over a
-run in which the pulse drives the electrons relativistically."""
+"""The two-species workloads at reduced size: the laser-plasma ones
+(a Gaussian pulse along y, a density ramp or an overdense foil, most
+supercells empty) and the KHI-like shear flow of the paper's evaluation:
+one-step parity with the FP64 oracle, and, for the laser cases, invariants
+over a run in which the pulse drives the electrons relativistically."""
 import numpy as np
 import pytest
 
@@ -26,7 +27,13 @@ def _foil_small():
                             foil=(60, 66), n_e_over_nc=30.0, pulse_gap=16.0)
 
 
-@pytest.mark.parametrize("make", [_laser_small, _foil_small], ids=["laser_ramp", "foil"])
+def _khi_small():
+    from paper_1606_02862_gb300 import workloads as W
+
+    return W.khi(n=16, ppc=4)
+
+
+@pytest.mark.parametrize("make", [_laser_small, _foil_small, _khi_small], ids=["laser_ramp", "foil", "khi"])
 def test_laser_workloads_one_step_parity(orc, make):
     require_gpu()
     wl = make()
