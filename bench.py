@@ -60,9 +60,10 @@ def measured_hbm():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def push_traffic_per_particle():
-    """DRAM bytes per particle of the push kernel from the committed ncu
-    summary, or None when the summary is absent or the kernel changed since."""
+def push_profile():
+    """Per-particle DRAM bytes and shared-memory wavefronts of the push kernel
+    from the committed ncu summary, or Nones when the summary is absent or the
+    kernel source changed since the counters were taken."""
     try:
         with open(PUSH_KERNEL_SRC, "rb") as f:
             sha = hashlib.sha256(f.read()).hexdigest()
@@ -73,10 +74,10 @@ def push_traffic_per_particle():
                     k, v = line.strip()[2:].split(":", 1)
                     vals[k.strip()] = v.strip().strip("`")
         if vals.get("k_push.cu sha256") != sha:
-            return None
-        return float(vals["dram bytes per particle"])
+            return None, None
+        return float(vals["dram bytes per particle"]), float(vals["shared wavefronts per particle"])
     except Exception:  # noqa: BLE001
-        return None
+        return None, None
 
 
 class ClockSampler:
@@ -132,6 +133,26 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- ours
+
+def binding_roofline(result, npart):
+    """The roofline that binds the TSC push kernel: shared-memory wavefronts
+    (ncu count per particle from the committed profile) per second against
+    one wavefront per cycle per SM at the SM clock sampled during the run."""
+    wpp = result.get("wpp")
+    mhz = (result.get("clocks") or {}).get("sm_mhz")
+    if not wpp or not mhz:
+        return None
+    try:
+        import torch
+
+        nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    except Exception:  # noqa: BLE001
+        return None
+    achieved = wpp * npart / (result["push_ms"] * 1e-3) / 1e9
+    peak = nsm * mhz * 1e6 / 1e9
+    return {"bound": "smem", "achieved": achieved, "peak": peak, "unit": "G wavefronts/s",
+            "frac": achieved / peak, "kernel": "k_push_deposit",
+            "per_particle": wpp, "peak_source": f"1 wavefront/clk/SM x {nsm} SMs x {mhz:.0f} MHz sampled"}
 
 def make_state(torch, n, ppc, u_th, pinned=True):
     from paper_1606_02862_gb300 import workloads as W
@@ -332,10 +353,10 @@ def run_ours(args, rank, world, dist):
     value = world * npart / (pd_ms_max * 1e-3)
     push_bytes = npart * MIXED_BYTES_PER_PARTICLE + ncell * MIXED_BYTES_PER_CELL
     achieved = push_bytes / (push_ms * 1e-3) / 1e9
-    tpp = push_traffic_per_particle()
+    tpp, wpp = push_profile()
     result.update(value=value, step_ms=step_ms_max, push_ms=push_ms, frames_ms=frames_ms,
                   yee_ms=yee_ms, graph=graph, kernels=kernels, achieved=achieved,
-                  traffic=None if tpp is None else tpp * npart, clocks=clk.summary())
+                  traffic=None if tpp is None else tpp * npart, clocks=clk.summary(), wpp=wpp)
     log(f"[rank {rank}] mixed: push {push_ms:.3f} ms, frames {frames_ms:.3f} ms, yee {yee_ms:.3f} ms,"
         f" step {step_ms:.3f} ms, graph={graph}")
 
@@ -412,6 +433,7 @@ def run_ours(args, rank, world, dist):
                      "frac": result["achieved"] / hbm, "traffic": result["traffic"],
                      "kernel": "k_push_deposit", "peak_source": hbm_src,
                      "bytes_per_launch": npart * MIXED_BYTES_PER_PARTICLE + ncell * MIXED_BYTES_PER_CELL},
+        "binding": binding_roofline(result, npart),
         "gpu_launches": int(result["kernels"] * args.steps),
         "clocks": result["clocks"],
     }
