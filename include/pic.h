@@ -86,7 +86,10 @@ typedef struct {
     int32_t threads_per_sc; /* CUDA threads per supercell work item (mixed form); 0 = cells per supercell */
     int32_t track_ids;      /* nonzero: carry a particle id (load order) through the frames */
     int32_t use_graph;      /* nonzero: pic_step replays a captured CUDA graph of one step */
-    int32_t reserved;
+    int32_t sort_every;     /* mixed form: every this many steps the push counting-sorts each frame
+                               list by nearest node (TSC) / cell (CIC) and writes it back in that
+                               order; the steps between push the lists in stored order; 0 = 4,
+                               1 = sort on every step (results agree up to FP32 summation order) */
     int64_t pool_frames;    /* frame-pool capacity (mixed); 0 = sized at the first step from the load */
     int64_t move_capacity;  /* capacity of the per-step buffer of particles changing supercell; 0 = auto */
     /* Device allocator.  Both NULL: cudaMalloc / cudaFree.  Otherwise every

@@ -116,8 +116,11 @@ __global__ void __launch_bounds__(1024) k_scan_top(const StepDev d, int nblk)
             s_carry = carry + tot;
         __syncthreads();
     }
-    if (threadIdx.x == 0)
+    if (threadIdx.x == 0) {
         *d.totals = s_carry;
+        if (d.step_ctr)
+            ++*d.step_ctr;
+    }
 }
 
 __global__ void __launch_bounds__(kScanThreads) k_scan_apply(const StepDev d)

@@ -382,8 +382,9 @@ struct SharedState {
     int off[max_keys<T>()];
     int holes[kHoleCap];
     int src[kHoleCap];
-    int item, any, ngen, nholes, nhead, nsrc;
-    unsigned bound_bits;  // float bits of the chunk's largest |jcoef w D|
+    int item, any, nholes, nhead, nsrc;
+    int ngen[2];             // general-window moves of the chunk
+    unsigned bound_bits[2];  // float bits of the chunk's largest |jcoef w D|
 };
 
 // ------------------------------------------------------------ deposit of one record
@@ -453,23 +454,122 @@ __device__ __forceinline__ void deposit_general(int* sJi, const Records<C>& r, i
                                           jc[1] * ws, jc[2] * ws);
 }
 
+// General window of one move, deposited by a whole warp (all 32 lanes
+// converged): lane 4a + k evaluates S0 and DS at node l - 1 + k of axis a and
+// the prefix P of DS along that axis; then each lane adds one or two of the
+// window's 48 lines (a component c and its transverse nodes p, q: three half
+// nodes along c), taking the factors it needs from the other lanes.
+template <class T, int SHAPE, int C>
+__device__ __forceinline__ void deposit_general_warp(int* sJi, const Records<C>& r, int s,
+                                                     const float jc[3], float scale)
+{
+    constexpr unsigned FULL = 0xffffffffu;
+    constexpr int PX = T::PX, PY = T::PX * T::TY, NJ = T::N;
+    const int lane = threadIdx.x & 31;
+    const int e = rslot(s);
+    const int l = r.l[e];
+    float s0v = 0.0f, dsv = 0.0f;
+    if (lane < 12) {
+        const int a = lane >> 2, k = lane & 3;
+        const float d0 = r.o[a][e] - (float)(k - 1);
+        const float D = r.D[a][e];
+        s0v = SHAPE == 2 ? tsc_S(d0) : cic_S(d0);
+        dsv = SHAPE == 2 ? tsc_dS(d0, D) : cic_dS(d0, D);
+    }
+    float pv = dsv;  // inclusive prefix over k within each group of 4 lanes
+    float t = __shfl_up_sync(FULL, pv, 1, 4);
+    if ((lane & 3) >= 1)
+        pv += t;
+    t = __shfl_up_sync(FULL, pv, 2, 4);
+    if ((lane & 3) >= 2)
+        pv += t;
+    const float ws = r.w[e] * scale;
+    const int b0 = l & 0xff, b1 = (l >> 8) & 0xff, b2 = (l >> 16) & 0xff;
+    const int base = b2 * PY + b1 * PX + b0;
+#pragma unroll
+    for (int round = 0; round < 2; ++round) {
+        const int L = lane + 32 * round;  // line: c = L / 16, p = L % 4, q = (L / 4) % 4
+        const int c = L >> 4;
+        const int ea = c == 2 ? 0 : c + 1, fa = c == 0 ? 2 : c - 1;  // transverse axes
+        const int p = L & 3, q = (L >> 2) & 3;
+        const int srcE = 4 * ea + p, srcF = 4 * fa + q;
+        const float s0e = __shfl_sync(FULL, s0v, srcE), dse = __shfl_sync(FULL, dsv, srcE);
+        const float s0f = __shfl_sync(FULL, s0v, srcF), dsf = __shfl_sync(FULL, dsv, srcF);
+        const float P0 = __shfl_sync(FULL, pv, 4 * (c & 3));
+        const float P1 = __shfl_sync(FULL, pv, 4 * (c & 3) + 1);
+        const float P2 = __shfl_sync(FULL, pv, 4 * (c & 3) + 2);
+        if (L < 48) {
+            const float cf = (c == 0 ? jc[0] : (c == 1 ? jc[1] : jc[2])) * ws;
+            const float Tv = cf * esk_T(s0e, dse, s0f, dsf);
+            const int st_c = c == 0 ? 1 : (c == 1 ? PX : PY);
+            const int st_e = ea == 0 ? 1 : (ea == 1 ? PX : PY);
+            const int st_f = fa == 0 ? 1 : (fa == 1 ? PX : PY);
+            int* at = sJi + c * NJ + base + p * st_e + q * st_f;
+            atomicAdd(at, magic_int(P0 * Tv));
+            atomicAdd(at + st_c, magic_int(P1 * Tv));
+            atomicAdd(at + 2 * st_c, magic_int(P2 * Tv));
+        }
+    }
+}
+
 // ------------------------------------------------------------ one particle
 
-// Pushes one particle; returns its bound |jcoef_d w D_d| on the current terms.
+// One particle in registers.
+struct Part {
+    int cell;
+    float o[3], u[3], w;
+};
+
+__device__ __forceinline__ Part load_part(const StepDev& d, int64_t idx)
+{
+    Part q;
+    q.cell = d.cell[idx];
+    q.o[0] = d.ox[idx];
+    q.o[1] = d.oy[idx];
+    q.o[2] = d.oz[idx];
+    q.u[0] = d.ux[idx];
+    q.u[1] = d.uy[idx];
+    q.u[2] = d.uz[idx];
+    q.w = d.w[idx];
+    return q;
+}
+
+// Writes a pushed particle to pool slot idx (only the cell of a leaver);
+// the weight only when the particle changed slot.
+__device__ __forceinline__ void store_part(const StepDev& d, int64_t idx, const Part& q, bool with_w)
+{
+    d.cell[idx] = q.cell;
+    if (q.cell >= 0) {
+        d.ox[idx] = q.o[0];
+        d.oy[idx] = q.o[1];
+        d.oz[idx] = q.o[2];
+        d.ux[idx] = q.u[0];
+        d.uy[idx] = q.u[1];
+        d.uz[idx] = q.u[2];
+        if (with_w)
+            d.w[idx] = q.w;
+    }
+}
+
+// Pushes one particle (gather, Boris, move) and writes its deposit record
+// at position sidx of the chunk; returns its bound |jcoef_d w D_d| on the
+// current terms.  A particle that stays in the supercell gets its new cell,
+// offsets and momentum in q; a leaver goes to the move buffer (its id read
+// from pidp when ids are tracked), q.cell becomes -1 and its list slot p
+// joins the hole list.
 template <class T, int SHAPE, int NT>
 __device__ __forceinline__ float push_one(const StepDev& d, const SpeciesDev& sp, int s, const BoxDev& bx,
                                          int scx, int scy, int scz, const float* sF,
-                                         SharedState<T, NT>& sh, int j, int p, int sidx,
-                                         unsigned& my_status)
+                                         SharedState<T, NT>& sh, Part& q, const int* pidp, int p,
+                                         int sidx, int cb, unsigned& my_status)
 {
     constexpr int LX = T::LX, LY = T::LY, LZ = T::LZ, N = T::N, PX = T::PX, TY = T::TY;
     constexpr int NW = SHAPE == 2 ? 3 : 2;
-    auto& st = sh.st;
     auto& rec = sh.rec;
-    const int cell = st.cell[j];
-    const float ox = st.o[0][j], oy = st.o[1][j], oz = st.o[2][j];
-    float ux = st.u[0][j], uy = st.u[1][j], uz = st.u[2][j];
-    const float w = st.w[j];
+    const int cell = q.cell;
+    const float ox = q.o[0], oy = q.o[1], oz = q.o[2];
+    float ux = q.u[0], uy = q.u[1], uz = q.u[2];
+    const float w = q.w;
     const int lx = cell % LX;
     const int ly = (cell / LX) % LY;
     const int lz = cell / (LX * LY);
@@ -522,7 +622,7 @@ __device__ __forceinline__ float push_one(const StepDev& d, const SpeciesDev& sp
     rec.D[2][rs] = Dz;
     rec.w[rs] = w;
     if (!common)
-        rec.gen[atomicAdd(&sh.ngen, 1)] = sidx;
+        rec.gen[atomicAdd(&sh.ngen[cb], 1)] = sidx;
     // bound on every current term of this particle: |jcoef_d w P| with |P| <= |D_d|
     // (P is a difference of cumulative shape sums, whose slope is at most 1),
     // times |T| <= (max S)^2: 9/16 for TSC (S <= 3/4), 1 for CIC
@@ -541,13 +641,13 @@ __device__ __forceinline__ float push_one(const StepDev& d, const SpeciesDev& sp
     const int dsy = nly < 0 ? -1 : (nly >= LY ? 1 : 0);
     const int dsz = nlz < 0 ? -1 : (nlz >= LZ ? 1 : 0);
     if ((dsx | dsy | dsz) == 0) {
-        st.cell[j] = nlx + LX * (nly + LY * nlz);
-        st.o[0][j] = nox;
-        st.o[1][j] = noy;
-        st.o[2][j] = noz;
-        st.u[0][j] = ux;
-        st.u[1][j] = uy;
-        st.u[2][j] = uz;
+        q.cell = nlx + LX * (nly + LY * nlz);
+        q.o[0] = nox;
+        q.o[1] = noy;
+        q.o[2] = noz;
+        q.u[0] = ux;
+        q.u[1] = uy;
+        q.u[2] = uz;
     } else {
         // leaves the supercell: into the move buffer, towards the neighbour
         // supercell (periodic within the box)
@@ -571,11 +671,11 @@ __device__ __forceinline__ float push_one(const StepDev& d, const SpeciesDev& sp
             d.mv_uz[m] = uz;
             d.mv_w[m] = w;
             if (d.pid)
-                d.mv_pid[m] = st.pid[j];
+                d.mv_pid[m] = *pidp;
         } else {
             my_status |= ST_CAPACITY;
         }
-        st.cell[j] = -1;
+        q.cell = -1;
         const int h = atomicAdd(&sh.nholes, 1);
         if (h < kHoleCap)
             sh.holes[h] = p;
@@ -603,7 +703,7 @@ template <class T, int SHAPE, int NT>
 __device__ __forceinline__ void push_list(const StepDev& d, const SpeciesDev& sp, int s, int g,
                                           const BoxDev& bx, int scx, int scy, int scz,
                                           const float* sF, int* sJi, float* sJf,
-                                          SharedState<T, NT>& sh, unsigned& my_status)
+                                          SharedState<T, NT>& sh, bool sort_pass, unsigned& my_status)
 {
     constexpr int LX = T::LX, LY = T::LY, S = T::S, N = T::N;
     constexpr int C = SharedState<T, NT>::C;
@@ -612,94 +712,127 @@ __device__ __forceinline__ void push_list(const StepDev& d, const SpeciesDev& sp
     const int L = s * d.nsc + g;
     const int n = d.count[L];
     const int* ft = d.ftab + d.foff[L];
+    auto gidx = [&](int slot) -> int64_t { return (int64_t)ft[slot >> d.log2S] * S + (slot & (S - 1)); };
     float prev_inv = 0.0f;
-    for (int base = 0; base < n; base += C) {
+    // chunk c uses the bound / general-list counters cb = c & 1; the other
+    // pair is cleared after the chunk's first barrier (its last readers were
+    // the previous chunk's deposits, its next writers come after the next
+    // chunk's last barrier)
+    int cb = 0;
+    for (int base = 0; base < n; base += C, cb ^= 1) {
         const int cn = min(C, n - base);
         if (base > 0)
-            fold_tile<N, NT>(sJi, sJf, prev_inv);  // previous chunk, disjoint from the staging below
-        for (int k = tid; k < K; k += NT)
-            sh.hist[k] = 0;
+            fold_tile<N, NT>(sJi, sJf, prev_inv);  // previous chunk; the push below does not touch J
+        if (sort_pass) {
+            // stage the chunk (coalesced), key = nearest node (TSC) / cell (CIC),
+            // then a counting sort; the pushed particles go back to the list
+            // in sorted order, so the list stays sorted by node between passes
+            for (int k = tid; k < K; k += NT)
+                sh.hist[k] = 0;
+            __syncthreads();
+            for (int j = tid; j < cn; j += NT) {
+                const int64_t idx = gidx(base + j);
+                const int cell = d.cell[idx];
+                const float ox = d.ox[idx], oy = d.oy[idx], oz = d.oz[idx];
+                sh.st.cell[j] = cell;
+                sh.st.o[0][j] = ox;
+                sh.st.o[1][j] = oy;
+                sh.st.o[2][j] = oz;
+                sh.st.u[0][j] = d.ux[idx];
+                sh.st.u[1][j] = d.uy[idx];
+                sh.st.u[2][j] = d.uz[idx];
+                sh.st.w[j] = d.w[idx];
+                if (d.pid)
+                    sh.st.pid[j] = d.pid[idx];
+                int key;
+                if (SHAPE == 2) {
+                    const int lx = cell % LX + (ox >= 0.5f), ly = (cell / LX) % LY + (oy >= 0.5f),
+                              lz = cell / (LX * LY) + (oz >= 0.5f);
+                    key = lx + (LX + 1) * (ly + (LY + 1) * lz);
+                } else {
+                    key = cell;
+                }
+                sh.st.kr[j] = (key << 16) | atomicAdd(&sh.hist[key], 1);
+            }
+            __syncthreads();
+            if (wid == 0)
+                warp_exclusive_scan_counts(sh.hist, sh.off, K);
+            __syncthreads();
+            for (int j = tid; j < cn; j += NT) {
+                const int kr = sh.st.kr[j];
+                sh.st.perm[sh.off[kr >> 16] + (kr & 0xffff)] = j;
+            }
+            __syncthreads();
+            // push in sorted order: neighbouring lanes read neighbouring field words
+            for (int s0 = 0; s0 < cn; s0 += NT) {
+                const int sidx = s0 + tid;
+                float bnd = 0.0f;
+                if (sidx < cn) {
+                    const int j = sh.st.perm[sidx];
+                    Part q;
+                    q.cell = sh.st.cell[j];
+                    q.o[0] = sh.st.o[0][j];
+                    q.o[1] = sh.st.o[1][j];
+                    q.o[2] = sh.st.o[2][j];
+                    q.u[0] = sh.st.u[0][j];
+                    q.u[1] = sh.st.u[1][j];
+                    q.u[2] = sh.st.u[2][j];
+                    q.w = sh.st.w[j];
+                    bnd = push_one<T, SHAPE, NT>(d, sp, s, bx, scx, scy, scz, sF, sh, q, sh.st.pid + j,
+                                                 base + sidx, sidx, cb, my_status);
+                    const int64_t idx = gidx(base + sidx);
+                    store_part(d, idx, q, true);
+                    if (d.pid && q.cell >= 0)
+                        d.pid[idx] = sh.st.pid[j];
+                }
+                const unsigned m = __reduce_max_sync(0xffffffffu, __float_as_uint(bnd));
+                if (lane == 0)
+                    atomicMax(&sh.bound_bits[cb], m);
+            }
+        } else {
+            // push in stored order (sorted at the last sort pass, a few
+            // particles displaced since): straight from the pool into
+            // registers and back to the same slot
+            for (int s0 = 0; s0 < cn; s0 += NT) {
+                const int sidx = s0 + tid;
+                float bnd = 0.0f;
+                if (sidx < cn) {
+                    const int64_t idx = gidx(base + sidx);
+                    Part q = load_part(d, idx);
+                    bnd = push_one<T, SHAPE, NT>(d, sp, s, bx, scx, scy, scz, sF, sh, q,
+                                                 d.pid ? d.pid + idx : nullptr, base + sidx, sidx, cb,
+                                                 my_status);
+                    store_part(d, idx, q, false);
+                }
+                const unsigned m = __reduce_max_sync(0xffffffffu, __float_as_uint(bnd));
+                if (lane == 0)
+                    atomicMax(&sh.bound_bits[cb], m);
+            }
+        }
+        __syncthreads();
         if (tid == 0) {
-            sh.ngen = 0;
-            sh.bound_bits = 0u;
+            sh.ngen[cb ^ 1] = 0;
+            sh.bound_bits[cb ^ 1] = 0u;
         }
-        __syncthreads();
-        // stage the chunk (coalesced), key = nearest node (TSC) / cell (CIC)
-        for (int j = tid; j < cn; j += NT) {
-            const int p = base + j;
-            const int64_t idx = (int64_t)ft[p >> d.log2S] * S + (p & (S - 1));
-            const int cell = d.cell[idx];
-            const float ox = d.ox[idx], oy = d.oy[idx], oz = d.oz[idx];
-            sh.st.cell[j] = cell;
-            sh.st.o[0][j] = ox;
-            sh.st.o[1][j] = oy;
-            sh.st.o[2][j] = oz;
-            sh.st.u[0][j] = d.ux[idx];
-            sh.st.u[1][j] = d.uy[idx];
-            sh.st.u[2][j] = d.uz[idx];
-            sh.st.w[j] = d.w[idx];
-            if (d.pid)
-                sh.st.pid[j] = d.pid[idx];
-            int key;
-            if (SHAPE == 2) {
-                const int lx = cell % LX + (ox >= 0.5f), ly = (cell / LX) % LY + (oy >= 0.5f),
-                          lz = cell / (LX * LY) + (oz >= 0.5f);
-                key = lx + (LX + 1) * (ly + (LY + 1) * lz);
-            } else {
-                key = cell;
-            }
-            sh.st.kr[j] = (key << 16) | atomicAdd(&sh.hist[key], 1);
-        }
-        __syncthreads();
-        if (wid == 0)
-            warp_exclusive_scan_counts(sh.hist, sh.off, K);
-        __syncthreads();
-        for (int j = tid; j < cn; j += NT) {
-            const int kr = sh.st.kr[j];
-            sh.st.perm[sh.off[kr >> 16] + (kr & 0xffff)] = j;
-        }
-        __syncthreads();
-        // push in sorted order: neighbouring lanes read neighbouring field words
-        for (int s0 = 0; s0 < cn; s0 += NT) {
-            const int sidx = s0 + tid;
-            float bnd = 0.0f;
-            if (sidx < cn) {
-                const int j = sh.st.perm[sidx];
-                bnd = push_one<T, SHAPE, NT>(d, sp, s, bx, scx, scy, scz, sF, sh, j, base + j, sidx,
-                                             my_status);
-            }
-            const unsigned m = __reduce_max_sync(0xffffffffu, __float_as_uint(bnd));
-            if (lane == 0)
-                atomicMax(&sh.bound_bits, m);
-        }
-        __syncthreads();
-        // deposit: lanes take sorted positions C/32 apart, so one warp's
+        // deposit: lanes take chunk positions C/32 apart, so one warp's
         // atomics land on different nodes; then the general-window moves
         float inv;
-        const float scale = chunk_scale(cn, __uint_as_float(sh.bound_bits), &inv);
+        const float scale = chunk_scale(cn, __uint_as_float(sh.bound_bits[cb]), &inv);
         for (int r = 0; r < C / NT; ++r) {
             const int e = lane * (C / 32) + wid * (C / NT) + r;
             if (e < cn && !(sh.rec.l[rslot(e)] >> 24))
                 deposit_common<T, SHAPE, C>(sJi, sh.rec, e, sp.jcoef, scale);
         }
-        const int ngen = sh.ngen;
-        for (int q = tid; q < ngen; q += NT)  // packed into as few warps as possible
+        // general-window moves: whole groups of 32 lane-parallel, one group
+        // per warp; the rest one move per warp, all lanes on it
+        const int ngen = sh.ngen[cb];
+        const int nfull = ngen & ~31;
+        for (int q = tid; q < nfull; q += NT)
             deposit_general<T, SHAPE, C>(sJi, sh.rec, sh.rec.gen[q], sp.jcoef, scale);
-        // write the chunk back (coalesced)
-        for (int j = tid; j < cn; j += NT) {
-            const int p = base + j;
-            const int64_t idx = (int64_t)ft[p >> d.log2S] * S + (p & (S - 1));
-            const int cell = sh.st.cell[j];
-            d.cell[idx] = cell;
-            if (cell >= 0) {
-                d.ox[idx] = sh.st.o[0][j];
-                d.oy[idx] = sh.st.o[1][j];
-                d.oz[idx] = sh.st.o[2][j];
-                d.ux[idx] = sh.st.u[0][j];
-                d.uy[idx] = sh.st.u[1][j];
-                d.uz[idx] = sh.st.u[2][j];
-            }
-        }
+        constexpr int NWARP = NT / 32;
+        const int rem = ngen - nfull;
+        for (int t = ((wid - (nfull >> 5)) % NWARP + NWARP) % NWARP; t < rem; t += NWARP)
+            deposit_general_warp<T, SHAPE, C>(sJi, sh.rec, sh.rec.gen[nfull + t], sp.jcoef, scale);
         prev_inv = inv;
         __syncthreads();
     }
@@ -803,6 +936,9 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_push_deposit(const StepDev d)
 
     const int tid = threadIdx.x;
     unsigned my_status = 0;
+    // every sort_every-th step reorders the lists (the counter only changes
+    // between launches, so all CTAs agree)
+    const bool sort_pass = d.sort_every <= 1 || (*d.step_ctr % d.sort_every) == 0;
 
     for (;;) {
         if (tid == 0)
@@ -865,13 +1001,16 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_push_deposit(const StepDev d)
             const int n = d.count[L];
             if (!sp.mobile || n == 0)
                 continue;
-            if (tid == 0)
+            if (tid == 0) {
                 sh.nholes = 0;
+                sh.ngen[0] = 0;
+                sh.bound_bits[0] = 0u;
+            }
             __syncthreads();
             if (sp.shape == 2)
-                push_list<T, 2, NT>(d, sp, s, g, bx, scx, scy, scz, sF, sJi, sJf, sh, my_status);
+                push_list<T, 2, NT>(d, sp, s, g, bx, scx, scy, scz, sF, sJi, sJf, sh, sort_pass, my_status);
             else
-                push_list<T, 1, NT>(d, sp, s, g, bx, scx, scy, scz, sF, sJi, sJf, sh, my_status);
+                push_list<T, 1, NT>(d, sp, s, g, bx, scx, scy, scz, sF, sJi, sJf, sh, sort_pass, my_status);
             const int nh = sh.nholes;
             if (nh > 0) {
                 compact_list<T, NT>(d, L, n, nh, sh.holes, sh.src, sh.nhead, sh.nsrc);

@@ -92,6 +92,8 @@ struct pic_ctx {
           *mv_uz = nullptr, *mv_w = nullptr;
     int4 *blk_sums = nullptr, *blk_offs = nullptr, *totals = nullptr;
     int* work_counter = nullptr;
+    int* step_ctr = nullptr;           // device step count, read by the push for its sort passes
+    int sort_every = kDefaultSortEvery;
     unsigned* wmax_bits = nullptr;     // [kMaxSpecies] device
     float wmax[kMaxSpecies] = {};      // host copy: largest |weight| per species
     int parity = 0;
@@ -337,6 +339,8 @@ StepDev make_step(const pic_ctx* c, int parity)
     d.blk_offs = c->blk_offs;
     d.totals = c->totals;
     d.work_counter = c->work_counter;
+    d.step_ctr = c->step_ctr;
+    d.sort_every = c->sort_every;
     d.status = c->status_d;
     d.wmax_bits = c->wmax_bits;
     return d;
@@ -736,7 +740,8 @@ pic_status pic_create(const pic_grid* grids, int32_t nboxes, const double dx[3],
     c->sp.assign(sp, sp + nspecies);
     c->rho_bg.assign(nboxes, 0.0);
     c->id_next.assign((size_t)nboxes * nspecies, 0);
-    if (c->precision != PIC_PRECISION_FP64_PLAIN && c->precision != PIC_PRECISION_MIXED) {
+    if ((c->precision != PIC_PRECISION_FP64_PLAIN && c->precision != PIC_PRECISION_MIXED) ||
+        o.sort_every < 0) {
         delete c;
         return PIC_ERR_ARG;
     }
@@ -790,6 +795,7 @@ pic_status pic_create(const pic_grid* grids, int32_t nboxes, const double dx[3],
         c->S = sc[0] * sc[1] * sc[2];
         c->log2S = ilog2(c->S);
         c->threads = o.threads_per_sc > 0 ? o.threads_per_sc : (c->S >= 256 ? 256 : 128);
+        c->sort_every = o.sort_every > 0 ? o.sort_every : kDefaultSortEvery;
         if ((1 << c->log2S) != c->S || !push_supported(c->LX, c->LY, c->LZ, c->threads))
             return bail(PIC_ERR_ARG);
         if (push_smem_bytes(c->LX, c->LY, c->LZ, c->threads) > c->smem_optin)
@@ -848,7 +854,7 @@ pic_status pic_create(const pic_grid* grids, int32_t nboxes, const double dx[3],
             dalloc(c, &c->free_top, 1) != PIC_OK || dalloc(c, &c->mv_count, 1) != PIC_OK ||
             dalloc(c, &c->blk_sums, nblk) != PIC_OK || dalloc(c, &c->blk_offs, nblk) != PIC_OK ||
             dalloc(c, &c->totals, 1) != PIC_OK || dalloc(c, &c->work_counter, 1) != PIC_OK ||
-            dalloc(c, &c->wmax_bits, kMaxSpecies) != PIC_OK)
+            dalloc(c, &c->step_ctr, 1) != PIC_OK || dalloc(c, &c->wmax_bits, kMaxSpecies) != PIC_OK)
             return bail(PIC_ERR_OOM);
         if (cudaMemcpyAsync(c->boxes_d, c->boxes_h.data(), sizeof(BoxDev) * nboxes,
                             cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
@@ -946,7 +952,11 @@ pic_status pic_load_particles(pic_ctx* c, int32_t box, int32_t species, int64_t 
                 CK(cudaStreamSynchronize(c->stream));
                 return fail(c, PIC_ERR_ARG, "non-finite particle data");
             }
-            // count the frames this insertion needs, grow the pool, then place
+            // count the frames this insertion needs, grow the pool, then place;
+            // the next step is a sort pass (the arrivals sit unsorted at the
+            // list ends)
+            d.step_ctr = nullptr;
+            CK(cudaMemsetAsync(c->step_ctr, 0, sizeof(int), c->stream));
             CK(launch_frame_plan(d, c->stream));
             int4 tot;
             int top = 0;

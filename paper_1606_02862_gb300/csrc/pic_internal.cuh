@@ -32,6 +32,7 @@
 namespace pic {
 
 constexpr int kMaxSpecies = 8;
+constexpr int kDefaultSortEvery = 4;  // steps between sort passes of the push (mixed form)
 
 // Device status word bits (OR-ed by kernels, read by the host after a step).
 enum : unsigned {
@@ -116,6 +117,8 @@ struct StepDev {
     int4* blk_offs;           // [scan blocks]
     int4* totals;             // device scalar: frames, alloc, release, -
     int* work_counter;        // persistent-kernel work counter
+    int* step_ctr;            // device step count (advanced by the frame plan)
+    int sort_every;           // the push sorts the frame lists every this many steps
     unsigned* status;         // device status word
     unsigned* wmax_bits;      // [kMaxSpecies] float bits of the largest |weight| loaded
 };

@@ -58,7 +58,7 @@ FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
 class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("sc", ctypes.c_int32 * 3),
                 ("threads_per_sc", ctypes.c_int32), ("track_ids", ctypes.c_int32),
-                ("use_graph", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("use_graph", ctypes.c_int32), ("sort_every", ctypes.c_int32),
                 ("pool_frames", ctypes.c_int64), ("move_capacity", ctypes.c_int64),
                 ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN), ("alloc_ud", ctypes.c_void_p),
                 ("stream", ctypes.c_void_p)]
@@ -156,7 +156,7 @@ class Context:
 
     def __init__(self, grids, dx, dt, species, precision=PRECISION_MIXED, sc=(4, 4, 4),
                  threads_per_sc=0, track_ids=False, use_graph=True, pool_frames=0,
-                 move_capacity=0, torch_memory=True):
+                 move_capacity=0, torch_memory=True, sort_every=0):
         L = library()
         self._L = L
         self._ctx = ctypes.c_void_p()
@@ -176,6 +176,7 @@ class Context:
         o.threads_per_sc = int(threads_per_sc)
         o.track_ids = int(bool(track_ids))
         o.use_graph = int(bool(use_graph))
+        o.sort_every = int(sort_every)
         o.pool_frames = int(pool_frames)
         o.move_capacity = int(move_capacity)
         self._mem = None

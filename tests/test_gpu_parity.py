@@ -47,10 +47,15 @@ def _thermal(n=(16, 16, 16), ppc=4, u_th=0.05, shape=2, seed=0, fields=1e-2, spe
     return W.Workload("thermal_test", W.DT_HALF_COURANT, sp, [box])
 
 
-def _one_step_parity(orc, wl, tol, **ctx_kw):
+def _one_step_parity(orc, wl, tol, pre_steps=0, **ctx_kw):
+    """pre_steps GPU steps first, then one compared step.  With the default
+    sort period of 4 the step after 0 pre-steps is a sort pass of the push
+    and the step after 1 to 3 pre-steps pushes the lists in stored order."""
     require_gpu()
     ctx = ctx_from(wl, **ctx_kw)
     try:
+        if pre_steps:
+            ctx.step(pre_steps)
         states = []
         for bi in range(len(wl.boxes)):
             st, ids = oracle_state_from_gpu(orc, ctx, wl, bi)
@@ -74,12 +79,23 @@ def test_plain_fp64_one_step(orc, shape):
     _one_step_parity(orc, wl, PLAIN_TOL, precision=pic.PRECISION_FP64_PLAIN)
 
 
+@pytest.mark.parametrize("pre", [0, 2], ids=["sort_pass", "stored_order"])
 @pytest.mark.parametrize("shape", [1, 2])
 @pytest.mark.parametrize("sc,threads", [((4, 4, 4), 64), ((4, 4, 4), 128), ((8, 8, 4), 128),
-                                        ((8, 8, 4), 256), ((8, 4, 4), 128), ((8, 8, 8), 256)])
-def test_mixed_one_step(orc, shape, sc, threads):
+                                        ((8, 8, 4), 256), ((8, 4, 4), 128), ((8, 4, 4), 256),
+                                        ((8, 8, 8), 256)])
+def test_mixed_one_step(orc, shape, sc, threads, pre):
     wl = _thermal(n=(16, 24, 16), shape=shape, u_th=0.1)
-    _one_step_parity(orc, wl, MIXED_TOL, sc=sc, threads_per_sc=threads)
+    _one_step_parity(orc, wl, MIXED_TOL, pre_steps=pre, sc=sc, threads_per_sc=threads)
+
+
+@pytest.mark.parametrize("sort_every", [1, 3])
+def test_mixed_sort_period(orc, sort_every):
+    """Every step a sort pass (1), or passes 1 and 2 in stored order after
+    a sort (3): the compared step is the one after two pre-steps."""
+    wl = _thermal(n=(16, 16, 16), shape=2, u_th=0.1, species="ions")
+    _one_step_parity(orc, wl, MIXED_TOL, pre_steps=2, sc=(8, 4, 4), threads_per_sc=256,
+                     sort_every=sort_every)
 
 
 def test_mixed_small_cic_workload(orc):
@@ -143,6 +159,7 @@ def test_mixed_edge_positions(orc):
     box = W.BoxInit(n, n, n, particles=[(x, u, np.full(x.shape[0], 0.05))], rho_bg=0.0)
     wl = W.Workload("edges", W.DT_HALF_COURANT, [W.SpeciesDef("e", -1.0, 1.0, 2)], [box])
     _one_step_parity(orc, wl, MIXED_TOL)
+    _one_step_parity(orc, wl, MIXED_TOL, pre_steps=1)
 
 
 def test_mixed_empty_and_lopsided_boxes(orc):
@@ -157,6 +174,7 @@ def test_mixed_empty_and_lopsided_boxes(orc):
                    E=rng.normal(0, 0.01, (3, 8, 8, 8)))
     wl = W.Workload("lopsided", W.DT_HALF_COURANT, [W.SpeciesDef("e", -1.0, 1.0, 2)], [b0, b1])
     _one_step_parity(orc, wl, MIXED_TOL)
+    _one_step_parity(orc, wl, MIXED_TOL, pre_steps=1)
 
 
 def test_plain_and_mixed_agree_after_one_step(orc):
