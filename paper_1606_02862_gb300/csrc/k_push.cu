@@ -23,13 +23,16 @@
 //                     * [S0y S0z + DSy S0z / 2 + S0y DSz / 2 + DSy DSz / 3](j, k)
 // i.e. an outer product of a prefix sum along x and a transverse factor.
 //
-// Particles are staged a chunk at a time in shared memory (coalesced loads
-// and stores) and pushed in the order of a counting sort by nearest node, so
-// the lanes of a warp read neighbouring field words (shared-memory
-// broadcasts).  The push writes a deposit record per particle; the deposit
-// then runs in a lane order whose neighbours are C/32 sorted positions apart,
-// so one warp's atomics land on different nodes.  The current of a chunk
-// accumulates in fixed point (see chunk_scale).
+// Particles go through a chunk of at most 256 at a time in the order of a
+// counting sort by nearest node, so the lanes of a warp read neighbouring
+// field words (shared-memory broadcasts).  Every sort_every-th step (a sort
+// pass) stages each chunk in shared memory, sorts it and writes it back to
+// the list in sorted order; the steps between push the lists in stored
+// order, straight from the pool into registers.  The push writes a deposit
+// record per particle; the deposit then runs in a lane order whose
+// neighbours are kDepStride sorted positions apart, so one warp's atomics
+// land on different nodes.  The current of a chunk accumulates in fixed
+// point (see chunk_scale).
 // Two deposit paths, both exact forms of that formula:
 //   common: on every axis the old and the new position round to the same
 //     node (TSC) / stay in the same cell (CIC), so the union of the two
@@ -48,6 +51,10 @@
 namespace pic {
 
 constexpr int kHoleCap = 256;
+// Lane stride of the deposit over the node-sorted chunk: 4 spreads one
+// warp's 54 atomics per particle over the banks better than 1 (neighbours
+// share a node) or C / 32 (random over the tile).
+constexpr int kDepStride = 4;
 
 template <int LX_, int LY_, int LZ_>
 struct Tile {
@@ -348,8 +355,9 @@ struct Stage {
 };
 
 // Deposit inputs of the chunk's moves, by sorted position s stored at slot
-// rslot(s) = s + s / 32: the deposit reads them with a stride of C / 32
-// between lanes, and the skew puts the 32 lanes on 32 different banks.
+// rslot(s) = s + s / 32: the deposit reads them with a stride of
+// kDepStride between lanes, and the skew puts the 32 lanes on 32 different
+// banks.
 __host__ __device__ constexpr int rslot(int s) { return s + (s >> 5); }
 
 template <int C>
@@ -814,12 +822,14 @@ __device__ __forceinline__ void push_list(const StepDev& d, const SpeciesDev& sp
             sh.ngen[cb ^ 1] = 0;
             sh.bound_bits[cb ^ 1] = 0u;
         }
-        // deposit: lanes take chunk positions C/32 apart, so one warp's
-        // atomics land on different nodes; then the general-window moves
+        // deposit: neighbouring lanes take chunk positions kDepStride apart
+        // (sorted by node, so one warp's atomics land on different nodes and
+        // mostly different banks); then the general-window moves
         float inv;
         const float scale = chunk_scale(cn, __uint_as_float(sh.bound_bits[cb]), &inv);
         for (int r = 0; r < C / NT; ++r) {
-            const int e = lane * (C / 32) + wid * (C / NT) + r;
+            const int q = r * NT + tid;
+            const int e = kDepStride * (q % (C / kDepStride)) + q / (C / kDepStride);
             if (e < cn && !(sh.rec.l[rslot(e)] >> 24))
                 deposit_common<T, SHAPE, C>(sJi, sh.rec, e, sp.jcoef, scale);
         }
