@@ -86,7 +86,7 @@ def lib():
             L.orc_deposit_esirkepov.restype = ctypes.c_int
             L.orc_push_deposit.argtypes = [gp, ctypes.c_double, ctypes.c_int, ctypes.c_double,
                                            ctypes.c_double, dp, dp, dp, ctypes.c_int64,
-                                           dp, dp, dp]
+                                           dp, dp, dp, ctypes.c_int]
             L.orc_push_deposit.restype = ctypes.c_int
             L.orc_yee_b.argtypes = [gp, ctypes.c_double, dp, dp]
             L.orc_yee_b.restype = None
@@ -103,6 +103,14 @@ def lib():
             L.orc_field_energy.restype = ctypes.c_double
             L.orc_kinetic_energy.argtypes = [ctypes.c_double, ctypes.c_int64, dp, dp]
             L.orc_kinetic_energy.restype = ctypes.c_double
+            L.orc_absorb_factor.argtypes = [ctypes.c_double] * 4
+            L.orc_absorb_factor.restype = ctypes.c_double
+            L.orc_absorb_y.argtypes = [gp, ctypes.c_double, ctypes.c_double, dp, dp]
+            L.orc_absorb_y.restype = None
+            L.orc_antenna_j0.argtypes = [ctypes.c_double] * 4 + [dp]
+            L.orc_antenna_j0.restype = ctypes.c_int
+            L.orc_antenna.argtypes = [gp, ctypes.c_int64] + [ctypes.c_double] * 9 + [dp]
+            L.orc_antenna.restype = ctypes.c_int
             _lib = L
     return _lib
 
@@ -172,6 +180,45 @@ def div_e(g: _Grid, E: np.ndarray) -> np.ndarray:
     return out
 
 
+def absorb_factor(y: float, ny: float, A: float, sigma: float) -> float:
+    """Damping factor of the y absorber at the (staggered) y position y."""
+    return lib().orc_absorb_factor(float(y), float(ny), float(A), float(sigma))
+
+
+def absorb_y(g: _Grid, A: float, sigma: float, E: np.ndarray, B: np.ndarray) -> None:
+    lib().orc_absorb_y(ctypes.byref(g), float(A), float(sigma), _ptr(E), _ptr(B))
+
+
+def antenna_j0(E0: float, omega: float, dt: float, dy: float = 1.0) -> float:
+    """Sheet current density that radiates a wave of amplitude E0 on the grid."""
+    out = np.zeros(1)
+    if lib().orc_antenna_j0(float(E0), float(omega), float(dt), float(dy), _ptr(out)) != ORC_OK:
+        raise ValueError("omega has no propagating wave on this grid")
+    return float(out[0])
+
+
+@dataclass
+class Antenna:
+    """Laser antenna on the node plane y = ja (Ex-polarised current sheet)."""
+    ja: int
+    E0: float
+    omega: float
+    w0: float = 0.0      # <= 0: plane sheet
+    xc: float = 0.0
+    zc: float = 0.0
+    tau: float = 0.0     # <= 0: no temporal envelope
+    t0: float = 0.0
+
+
+def antenna(g: _Grid, a: Antenna, dt: float, t: float, J: np.ndarray) -> None:
+    """Add the antenna's current at time t (the half step) into J."""
+    rc = lib().orc_antenna(ctypes.byref(g), int(a.ja), float(a.E0), float(a.omega), float(a.w0),
+                           float(a.xc), float(a.zc), float(a.tau), float(a.t0), float(dt), float(t),
+                           _ptr(J))
+    if rc != ORC_OK:
+        raise ValueError("omega has no propagating wave on this grid")
+
+
 def yee_b(g: _Grid, tau: float, E: np.ndarray, B: np.ndarray) -> None:
     lib().orc_yee_b(ctypes.byref(g), float(tau), _ptr(E), _ptr(B))
 
@@ -203,8 +250,13 @@ class Species:
 
 @dataclass
 class State:
-    """One periodic box: fields, species, and a fixed uniform background
-    charge density rho_bg (it adds to rho and carries no current)."""
+    """One box: fields, species, and a fixed uniform background charge
+    density rho_bg (it adds to rho and carries no current).  Periodic unless
+    the open-y options are set:
+      absorber = (A, sigma): damping layers of A cells at both y faces;
+      open_y: particles that leave through a y face are removed;
+      antenna: a laser antenna (Antenna) driven at the half steps;
+    t is the time of E (advanced by dt per step)."""
     nx: int
     ny: int
     nz: int
@@ -215,6 +267,10 @@ class State:
     J: np.ndarray | None = None
     species: list = field(default_factory=list)
     rho_bg: float = 0.0
+    absorber: tuple | None = None
+    open_y: bool = False
+    antenna: Antenna | None = None
+    t: float = 0.0
 
     def __post_init__(self):
         shp = (3, self.nz, self.ny, self.nx)
@@ -224,7 +280,10 @@ class State:
         self.g = grid(self.nx, self.ny, self.nz, self.dx)
 
     def step(self, nsteps: int = 1) -> None:
-        """Advance nsteps full PIC cycles in the order of the module docstring."""
+        """Advance nsteps full PIC cycles in the order of the module docstring;
+        with the open-y options: particles that left through a y face are
+        removed after their deposit, the antenna current joins J before the
+        field update, and the absorber damps E and B after it."""
         L = lib()
         for _ in range(nsteps):
             self.J[...] = 0.0
@@ -234,11 +293,47 @@ class State:
                 rc = L.orc_push_deposit(ctypes.byref(self.g), float(self.dt), int(sp.order),
                                         float(sp.q), float(sp.m), _ptr(self.E), _ptr(self.B),
                                         _ptr(self.J), int(sp.x.shape[0]), _ptr(sp.x), _ptr(sp.u),
-                                        _ptr(sp.w))
+                                        _ptr(sp.w), int(bool(self.open_y)))
                 if rc != ORC_OK:
                     raise ValueError(f"oracle push rejected a particle move (code {rc})")
+                if self.open_y:
+                    keep = (sp.x[:, 1] >= 0.0) & (sp.x[:, 1] < float(self.ny))
+                    if not np.all(keep):
+                        sp.x = np.ascontiguousarray(sp.x[keep])
+                        sp.u = np.ascontiguousarray(sp.u[keep])
+                        if sp.w is not None:
+                            sp.w = np.ascontiguousarray(sp.w[keep])
+                        if getattr(sp, "ids", None) is not None:
+                            sp.ids = sp.ids[keep]
+            if self.antenna is not None:
+                antenna(self.g, self.antenna, self.dt, self.t + 0.5 * self.dt, self.J)
             L.orc_yee_step(ctypes.byref(self.g), float(self.dt), _ptr(self.E), _ptr(self.B),
                            _ptr(self.J))
+            if self.absorber is not None:
+                absorb_y(self.g, self.absorber[0], self.absorber[1], self.E, self.B)
+            self.t += self.dt
+
+    def shift_window(self, cells: int) -> None:
+        """Moving window: the box moves `cells` cells towards +y.  Field values
+        move down by `cells` planes and the planes that enter at the top are
+        zero; particle y coordinates drop by `cells` and the particles that
+        leave through the bottom are removed.  Fresh plasma for the top is
+        the caller's to load."""
+        m = int(cells)
+        if not 0 < m < self.ny:
+            raise ValueError("shift must be in (0, ny)")
+        for F in (self.E, self.B, self.J):
+            F[:, :, :self.ny - m, :] = F[:, :, m:, :].copy()
+            F[:, :, self.ny - m:, :] = 0.0
+        for sp in self.species:
+            sp.x[:, 1] -= float(m)
+            keep = sp.x[:, 1] >= 0.0
+            sp.x = np.ascontiguousarray(sp.x[keep])
+            sp.u = np.ascontiguousarray(sp.u[keep])
+            if sp.w is not None:
+                sp.w = np.ascontiguousarray(sp.w[keep])
+            if getattr(sp, "ids", None) is not None:
+                sp.ids = sp.ids[keep]
 
     def rho(self) -> np.ndarray:
         """Charge density at the nodes, background included."""

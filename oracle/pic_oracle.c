@@ -210,11 +210,14 @@ int orc_deposit_esirkepov(const orc_grid* g, int order, double qw, double dt,
  * One particle species through gather -> Boris -> move -> Esirkepov (the
  * particle half of the PIC cycle, Sec. 2.1 and Sec. 4).  x is n x 3 in cell
  * units and is wrapped back into [0, N) after the move; u is n x 3; w is n
- * (NULL = all weights 1).  J accumulates (the caller zeroes it).
+ * (NULL = all weights 1).  J accumulates (the caller zeroes it).  open_y:
+ * the y coordinate is not wrapped, so that the caller can remove the
+ * particles that left through a y face (they have deposited their current,
+ * folded periodically like every other deposit).
  */
 int orc_push_deposit(const orc_grid* g, double dt, int order, double q, double m,
                      const double* E, const double* B, double* J,
-                     int64_t n, double* x, double* u, const double* w)
+                     int64_t n, double* x, double* u, const double* w, int open_y)
 {
     double h[3] = {g->dx, g->dy, g->dz};
     int64_t N[3] = {g->nx, g->ny, g->nz};
@@ -234,6 +237,10 @@ int orc_push_deposit(const orc_grid* g, double dt, int order, double q, double m
             return rc;
         for (int d = 0; d < 3; ++d) {
             double y = x1[d];
+            if (d == 1 && open_y) { /* left for the caller to remove when outside [0, ny) */
+                xp[d] = y;
+                continue;
+            }
             if (y >= (double)N[d])
                 y -= (double)N[d];
             else if (y < 0.0)
@@ -371,4 +378,89 @@ double orc_kinetic_energy(double m, int64_t n, const double* u, const double* w)
         s += (w ? w[p] : 1.0) * m * gm1;
     }
     return s;
+}
+
+/*
+ * ---------------------------------------------------------------- open y
+ * Boundaries along y for the laser-plasma setups (the paper's own runs are
+ * periodic and it names no boundary scheme; these are the readings the
+ * tests and the CUDA path share):
+ *
+ * Absorber: damping layers of A cells at both y faces.  After each full
+ * field step every E and B component is multiplied by exp(-sigma delta^2),
+ * delta in [0, 1] being the depth of the component's staggered y position
+ * inside the layer, from 0 at the layer's inner edge to 1 at the face:
+ * delta = (A - y) / A for y < A, (y - (ny - A)) / A for y > ny - A.
+ */
+double orc_absorb_factor(double y, double ny, double A, double sigma)
+{
+    double depth = 0.0;
+    if (A <= 0.0)
+        return 1.0;
+    if (y < A)
+        depth = (A - y) / A;
+    else if (y > ny - A)
+        depth = (y - (ny - A)) / A;
+    if (depth > 1.0)
+        depth = 1.0;
+    return exp(-sigma * depth * depth);
+}
+
+void orc_absorb_y(const orc_grid* g, double A, double sigma, double* E, double* B)
+{
+    int64_t nc = ncells(g);
+    for (int c = 0; c < 3; ++c)
+        for (int64_t k = 0; k < g->nz; ++k)
+            for (int64_t j = 0; j < g->ny; ++j) {
+                double fe = orc_absorb_factor((double)j + E_STAGGER[c][1], (double)g->ny, A, sigma);
+                double fb = orc_absorb_factor((double)j + B_STAGGER[c][1], (double)g->ny, A, sigma);
+                for (int64_t i = 0; i < g->nx; ++i) {
+                    int64_t idx = c * nc + cell_index(g, i, j, k);
+                    E[idx] *= fe;
+                    B[idx] *= fb;
+                }
+            }
+}
+
+/*
+ * Laser antenna: a sheet of current along x on the node plane j = ja (the
+ * Ex positions (i+1/2, ja, k)), added to J at the time t of the current
+ * (t = (n + 1/2) dt for the step from n to n+1):
+ *   Jx += J0 G(x, z) T(t) cos(omega (t - t0)),
+ *   G = exp(-((x - xc)^2 + (z - zc)^2) / w0^2),  T = exp(-((t - t0) / tau)^2),
+ *   J0 = -2 E0 cos(kappa / 2) / dy,
+ * kappa being the wavenumber (per cell along y) that the Yee dispersion
+ * relation gives for omega: sin(kappa / 2) = (dy / dt) sin(omega dt / 2).
+ * On the Yee grid a sheet of surface current K oscillating at omega radiates
+ * Ex = -K / (2 cos(kappa / 2)) to either side, so the plane wave leaving the
+ * sheet has amplitude E0.  w0 <= 0: no transverse envelope (a plane sheet);
+ * tau <= 0: no temporal envelope.  Returns ORC_ERR_ARG when omega has no
+ * propagating wave on the grid.
+ */
+int orc_antenna_j0(double E0, double omega, double dt, double dy, double* J0)
+{
+    double sk = (dy / dt) * sin(0.5 * omega * dt);
+    if (!(fabs(sk) < 1.0))
+        return ORC_ERR_ARG;
+    double kappa = 2.0 * asin(sk);
+    *J0 = -2.0 * E0 * cos(0.5 * kappa) / dy;
+    return ORC_OK;
+}
+
+int orc_antenna(const orc_grid* g, int64_t ja, double E0, double omega, double w0, double xc,
+                double zc, double tau, double t0, double dt, double t, double* J)
+{
+    double J0;
+    if (orc_antenna_j0(E0, omega, dt, g->dy, &J0) != ORC_OK)
+        return ORC_ERR_ARG;
+    double T = tau > 0.0 ? exp(-((t - t0) / tau) * ((t - t0) / tau)) : 1.0;
+    double amp = J0 * T * cos(omega * (t - t0));
+    for (int64_t k = 0; k < g->nz; ++k)
+        for (int64_t i = 0; i < g->nx; ++i) {
+            double x = ((double)i + 0.5) * g->dx, z = (double)k * g->dz;
+            double r2 = (x - xc) * (x - xc) + (z - zc) * (z - zc);
+            double G = w0 > 0.0 ? exp(-r2 / (w0 * w0)) : 1.0;
+            J[cell_index(g, i, ja, k)] += amp * G;
+        }
+    return ORC_OK;
 }
