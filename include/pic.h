@@ -130,6 +130,63 @@ pic_status pic_create(const pic_grid* grids, int32_t nboxes, const double dx[3],
 pic_status pic_set_background(pic_ctx* ctx, int32_t box, double rho_bg);
 
 /*
+ * Open boundaries along y (mixed form only; the plain form returns
+ * PIC_ERR_ARG).  The paper's own runs are periodic; these are the boundary
+ * steps of laser-plasma runs, on either side of the hot path.  The grid stays
+ * periodic in its indexing (guards hold periodic images); the options act on
+ * top of it.
+ *
+ * pic_set_boundary -- per box:
+ *   open_y          nonzero: a particle that leaves through a y face is removed
+ *                   at the end of its push (its current of that step is
+ *                   deposited, folded periodically like every deposit);
+ *   absorber_cells  A >= 0: damping layers of A cells at both y faces.  After
+ *                   every field update each E and B component is multiplied
+ *                   by exp(-sigma d^2), d in [0, 1] being the depth of its
+ *                   staggered y position in the layer (0 at the layer's inner
+ *                   edge, 1 at the face);
+ *   absorber_sigma  sigma >= 0.
+ * 2 A <= ny.  Takes effect from the next step.
+ */
+typedef struct {
+    int32_t open_y;
+    int32_t absorber_cells;
+    double absorber_sigma;
+} pic_boundary;
+pic_status pic_set_boundary(pic_ctx* ctx, int32_t box, const pic_boundary* b);
+
+/*
+ * pic_set_antenna -- a laser antenna in box `box`: a sheet of current along x
+ * on the node plane y = plane_y (the Ex positions (i+1/2, plane_y, k)), added
+ * to J before the E update of every step at the current's time
+ * t = (n + 1/2) dt (n = steps taken before this one):
+ *   Jx += J0 exp(-((x - xc)^2 + (z - zc)^2) / w0^2) exp(-((t - t0)/tau)^2)
+ *            cos(omega (t - t0)),
+ *   J0 = -2 E0 cos(kappa/2) / dy,  sin(kappa/2) = (dy/dt) sin(omega dt/2),
+ * so that on the Yee grid the wave leaving the sheet (to both sides) has
+ * amplitude E0.  x, z, xc, zc, w0 in cell units times dx, dz; w0 <= 0: a plane
+ * sheet; tau <= 0: no temporal envelope.  plane_y < 0 removes the antenna.
+ * PIC_ERR_ARG when omega has no propagating wave on the grid
+ * ((dy/dt) |sin(omega dt/2)| >= 1) or plane_y >= ny.
+ */
+typedef struct {
+    int32_t plane_y;
+    int32_t reserved;
+    double E0, omega, w0, xc, zc, tau, t0;
+} pic_antenna;
+pic_status pic_set_antenna(pic_ctx* ctx, int32_t box, const pic_antenna* a);
+
+/*
+ * pic_shift_window -- moving window: box `box` moves `cells` cells towards +y.
+ * Field values move down by `cells` planes, the planes entering at the top are
+ * zero, particle y coordinates drop by `cells` and the particles of the bottom
+ * `cells` planes are removed.  `cells` must be a positive multiple of the
+ * supercell edge along y, below ny.  Fresh plasma for the top is the caller's
+ * to load (pic_load_particles).
+ */
+pic_status pic_shift_window(pic_ctx* ctx, int32_t box, int32_t cells);
+
+/*
  * pic_load_particles -- append n particles of species `species` to box `box`.
  *   x[n*3]  global positions in cell units (host, FP64); wrapped
  *           periodically into [0, N) on load.
@@ -216,14 +273,16 @@ pic_status pic_stage_times(pic_ctx* ctx, double ms[4], int64_t* nsteps_out);
  *   PIC_INFO_KERNELS_PER_STEP number of libpic kernel launches one step makes;
  *   PIC_INFO_POOL_FRAMES     frame-pool capacity (mixed form);
  *   PIC_INFO_FRAMES_USED     frames holding particles, read from the device;
- *   PIC_INFO_MOVE_CAPACITY   capacity of the per-step buffer of particles changing supercell.
+ *   PIC_INFO_MOVE_CAPACITY   capacity of the per-step buffer of particles changing supercell;
+ *   PIC_INFO_STEPS           steps taken since pic_create (the time of E is STEPS * dt).
  */
 enum {
     PIC_INFO_GRAPH_ACTIVE = 0,
     PIC_INFO_KERNELS_PER_STEP = 1,
     PIC_INFO_POOL_FRAMES = 2,
     PIC_INFO_FRAMES_USED = 3,
-    PIC_INFO_MOVE_CAPACITY = 4
+    PIC_INFO_MOVE_CAPACITY = 4,
+    PIC_INFO_STEPS = 5
 };
 pic_status pic_info(pic_ctx* ctx, int32_t key, int64_t* out);
 

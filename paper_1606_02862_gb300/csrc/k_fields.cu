@@ -28,6 +28,9 @@ struct YeeArgs {
     int nboxes;
     float tau;           // dt/2 for the B halves, dt for E
     float ih[3];         // 1 / h_d
+    const long long* step_no;
+    double dt_d;
+    double dx_d[3];
 };
 
 __device__ __forceinline__ int find_box(const int* off, int n, int blk)
@@ -109,6 +112,24 @@ __global__ void __launch_bounds__(256) k_yee_b(const YeeArgs a)
     store_with_images(b, Bz, c, Bz[i] - a.tau * cz);
 }
 
+// Laser antenna: the sheet current at the Ex position (x+1/2, ant_j, z) at
+// the time of this step's current, t = (n + 1/2) dt, n = steps taken before
+// it (step_no was advanced earlier in the step).  FP64 throughout: omega t
+// reaches thousands of radians.
+__device__ __forceinline__ float antenna_current(const YeeArgs& a, const BoxDev& b, int x, int z)
+{
+    const OpenYDev& o = b.oy;
+    const double t = ((double)(*a.step_no) - 0.5) * a.dt_d;
+    const double T = o.ant_tau > 0.0 ? exp(-((t - o.ant_t0) / o.ant_tau) * ((t - o.ant_t0) / o.ant_tau)) : 1.0;
+    double G = 1.0;
+    if (o.ant_w0 > 0.0) {
+        const double px = ((double)x + 0.5) * a.dx_d[0] - o.ant_xc;
+        const double pz = (double)z * a.dx_d[2] - o.ant_zc;
+        G = exp(-(px * px + pz * pz) / (o.ant_w0 * o.ant_w0));
+    }
+    return (float)(o.ant_J0 * G * T * cos(o.ant_omega * (t - o.ant_t0)));
+}
+
 __global__ void __launch_bounds__(256) k_yee_e(const YeeArgs a)
 {
     BoxDev b;
@@ -135,6 +156,8 @@ __global__ void __launch_bounds__(256) k_yee_e(const YeeArgs a)
                     b.J[2 * pc + g] = 0.f;
                 }
             }
+    if (c.y == b.oy.ant_j)
+        jx += antenna_current(a, b, c.x, c.z);
     b.J[i] = jx;
     b.J[pc + i] = jy;
     b.J[2 * pc + i] = jz;
@@ -149,15 +172,97 @@ __global__ void __launch_bounds__(256) k_yee_e(const YeeArgs a)
     store_with_images(b, Ez, c, Ez[i] + a.tau * (cz - jz));
 }
 
+// y absorber: every E and B value whose staggered y position lies in a
+// damping layer is multiplied by exp(-sigma d^2) (d = depth in the layer, 0
+// at its inner edge, 1 at the face), images included.  Work: the 2A planes
+// j < A and j >= ny - A of each box with a layer, 256 cells per block.
+__device__ __forceinline__ float absorb_factor(float y, int ny, int A, float sigma)
+{
+    float depth = 0.0f;
+    if (y < (float)A)
+        depth = ((float)A - y) / (float)A;
+    else if (y > (float)(ny - A))
+        depth = (y - (float)(ny - A)) / (float)A;
+    depth = fminf(depth, 1.0f);
+    return expf(-sigma * depth * depth);
+}
+
+int absorber_blocks(const BoxDev& b)
+{
+    const int A = b.oy.abs_cells;
+    if (A <= 0)
+        return 0;
+    const int64_t cells = (int64_t)2 * A * b.nx * b.nz;
+    return (int)((cells + 255) / 256);
+}
+
+__global__ void __launch_bounds__(256) k_absorb_y(const BoxDev* boxes, const int* off, int nboxes)
+{
+    const int box = find_box(off, nboxes, blockIdx.x);
+    const BoxDev b = boxes[box];
+    const int A = b.oy.abs_cells;
+    const int64_t t = (int64_t)(blockIdx.x - off[box]) * 256 + threadIdx.x;
+    if (A <= 0 || t >= (int64_t)2 * A * b.nx * b.nz)
+        return;
+    CellAt c;
+    c.x = (int)(t % b.nx);
+    const int p = (int)((t / b.nx) % (2 * A));
+    c.z = (int)(t / ((int64_t)b.nx * 2 * A));
+    c.y = p < A ? p : b.ny - 2 * A + p;
+    c.ok = true;
+    const int64_t pc = padded_cells(b);
+    const int64_t i = padded_index(b, c.x, c.y, c.z);
+    const float s = b.oy.abs_sigma;
+    const float fi = absorb_factor((float)c.y, b.ny, A, s);          // Ex, Ez, By
+    const float fh = absorb_factor((float)c.y + 0.5f, b.ny, A, s);   // Ey, Bx, Bz
+    store_with_images(b, b.E, c, b.E[i] * fi);
+    store_with_images(b, b.E + pc, c, b.E[pc + i] * fh);
+    store_with_images(b, b.E + 2 * pc, c, b.E[2 * pc + i] * fi);
+    store_with_images(b, b.B, c, b.B[i] * fh);
+    store_with_images(b, b.B + pc, c, b.B[pc + i] * fi);
+    store_with_images(b, b.B + 2 * pc, c, b.B[2 * pc + i] * fh);
+}
+
 cudaError_t launch_yee_mixed_plan(const YeePlan& p, cudaStream_t st)
 {
-    YeeArgs a{p.boxes, p.blk_off, p.nboxes, 0.5f * p.dt, {p.ih[0], p.ih[1], p.ih[2]}};
+    YeeArgs a{p.boxes, p.blk_off, p.nboxes, 0.5f * p.dt, {p.ih[0], p.ih[1], p.ih[2]},
+              p.step_no, p.dt_d, {p.dx_d[0], p.dx_d[1], p.dx_d[2]}};
     dim3 blk(32, 8);
     k_yee_b<<<p.nblocks, blk, 0, st>>>(a);
     a.tau = p.dt;
     k_yee_e<<<p.nblocks, blk, 0, st>>>(a);
     a.tau = 0.5f * p.dt;
     k_yee_b<<<p.nblocks, blk, 0, st>>>(a);
+    if (p.abs_nblocks > 0)
+        k_absorb_y<<<p.abs_nblocks, 256, 0, st>>>(p.boxes, p.abs_off, p.nboxes);
+    return cudaGetLastError();
+}
+
+// Moving window: F (3 components) takes the values of scratch (a copy of F)
+// `cells` planes higher; the planes entering at the top are zero; images
+// rewritten.
+__global__ void k_shift_fields(const BoxDev b, float* F, const float* scratch, int cells)
+{
+    const int64_t n = (int64_t)b.nx * b.ny * b.nz;
+    const int64_t pc = padded_cells(b);
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < 3 * n;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int comp = (int)(t / n);
+        const int64_t r = t - comp * n;
+        CellAt c;
+        c.x = (int)(r % b.nx);
+        c.y = (int)((r / b.nx) % b.ny);
+        c.z = (int)(r / ((int64_t)b.nx * b.ny));
+        c.ok = true;
+        const float v = c.y + cells < b.ny ? scratch[comp * pc + padded_index(b, c.x, c.y + cells, c.z)] : 0.0f;
+        store_with_images(b, F + comp * pc, c, v);
+    }
+}
+
+cudaError_t launch_shift_fields(const BoxDev& b, float* F, const float* scratch, int cells,
+                                cudaStream_t st)
+{
+    k_shift_fields<<<1024, 256, 0, st>>>(b, F, scratch, cells);
     return cudaGetLastError();
 }
 

@@ -118,8 +118,10 @@ __global__ void __launch_bounds__(1024) k_scan_top(const StepDev d, int nblk)
     }
     if (threadIdx.x == 0) {
         *d.totals = s_carry;
-        if (d.step_ctr)
+        if (d.step_ctr) {
             ++*d.step_ctr;
+            ++*d.step_no;
+        }
     }
 }
 
@@ -206,6 +208,56 @@ __global__ void __launch_bounds__(1024) k_free_push(const StepDev d)
         *d.free_top = base + tot.z;
         *d.mv_count = 0;
     }
+}
+
+// Moving window, part 1: empty the lists of the bottom `rows` supercell
+// rows of a box (every species); the next maintenance pass releases their
+// frames.
+__global__ void k_clear_rows(const StepDev d, const BoxDev b, int rows)
+{
+    const int per_species = b.nscx * rows * b.nscz;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < d.nspecies * per_species;
+         t += gridDim.x * blockDim.x) {
+        const int s = t / per_species, r = t % per_species;
+        const int scx = r % b.nscx, scy = (r / b.nscx) % rows, scz = r / (b.nscx * rows);
+        d.count[s * d.nsc + b.sc_base + (scz * b.nscy + scy) * b.nscx + scx] = 0;
+    }
+}
+
+// Moving window, part 2: the list of row scy takes over the list (count,
+// frames, frame-table offset) of row scy + rows, cyclically; the rows that
+// were emptied in part 1 come round to the top.  old3 = copies of count,
+// nframes and foff (nlists each), taken before the kernel.
+__global__ void k_rotate_lists(const StepDev d, const BoxDev b, const int* old3, int* foff, int rows)
+{
+    const int nbox = b.nscx * b.nscy * b.nscz;
+    const int* count_old = old3;
+    const int* nframes_old = old3 + d.nlists;
+    const int* foff_old = old3 + 2 * d.nlists;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < d.nspecies * nbox;
+         t += gridDim.x * blockDim.x) {
+        const int s = t / nbox, loc = t % nbox;
+        const int scx = loc % b.nscx, scy = (loc / b.nscx) % b.nscy, scz = loc / (b.nscx * b.nscy);
+        const int sy = (scy + rows) % b.nscy;
+        const int L = s * d.nsc + b.sc_base + loc;
+        const int Ls = s * d.nsc + b.sc_base + (scz * b.nscy + sy) * b.nscx + scx;
+        d.count[L] = count_old[Ls];
+        d.nframes[L] = nframes_old[Ls];
+        foff[L] = foff_old[Ls];
+    }
+}
+
+cudaError_t launch_clear_rows(const StepDev& d, const BoxDev& hb, int rows, cudaStream_t st)
+{
+    k_clear_rows<<<256, 256, 0, st>>>(d, hb, rows);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rotate_lists(const StepDev& d, const BoxDev& hb, const int* old3, int* foff,
+                                int rows, cudaStream_t st)
+{
+    k_rotate_lists<<<256, 256, 0, st>>>(d, hb, old3, foff, rows);
+    return cudaGetLastError();
 }
 
 int frame_scan_blocks(int nlists) { return (nlists + kScanTile - 1) / kScanTile; }

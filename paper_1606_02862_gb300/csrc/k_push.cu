@@ -658,30 +658,33 @@ __device__ __forceinline__ float push_one(const StepDev& d, const SpeciesDev& sp
         q.u[2] = uz;
     } else {
         // leaves the supercell: into the move buffer, towards the neighbour
-        // supercell (periodic within the box)
+        // supercell (periodic within the box), or, through a y face of an
+        // open-y box, out of the simulation
         int tsx = scx + dsx, tsy = scy + dsy, tsz = scz + dsz;
-        tsx += tsx < 0 ? bx.nscx : (tsx >= bx.nscx ? -bx.nscx : 0);
-        tsy += tsy < 0 ? bx.nscy : (tsy >= bx.nscy ? -bx.nscy : 0);
-        tsz += tsz < 0 ? bx.nscz : (tsz >= bx.nscz ? -bx.nscz : 0);
-        const int dest_sc = bx.sc_base + (tsz * bx.nscy + tsy) * bx.nscx + tsx;
-        const int dest_cell = (nlx - dsx * LX) + LX * ((nly - dsy * LY) + LY * (nlz - dsz * LZ));
-        const int destL = s * d.nsc + dest_sc;
-        const int m = warp_aggregated_add(d.mv_count);
-        if (m < d.mv_cap) {
-            d.mv_rank[m] = atomicAdd(d.narrive + destL, 1);
-            d.mv_dest[m] = destL;
-            d.mv_cell[m] = dest_cell;
-            d.mv_ox[m] = nox;
-            d.mv_oy[m] = noy;
-            d.mv_oz[m] = noz;
-            d.mv_ux[m] = ux;
-            d.mv_uy[m] = uy;
-            d.mv_uz[m] = uz;
-            d.mv_w[m] = w;
-            if (d.pid)
-                d.mv_pid[m] = *pidp;
-        } else {
-            my_status |= ST_CAPACITY;
+        if (!(bx.oy.open_y && (tsy < 0 || tsy >= bx.nscy))) {
+            tsx += tsx < 0 ? bx.nscx : (tsx >= bx.nscx ? -bx.nscx : 0);
+            tsy += tsy < 0 ? bx.nscy : (tsy >= bx.nscy ? -bx.nscy : 0);
+            tsz += tsz < 0 ? bx.nscz : (tsz >= bx.nscz ? -bx.nscz : 0);
+            const int dest_sc = bx.sc_base + (tsz * bx.nscy + tsy) * bx.nscx + tsx;
+            const int dest_cell = (nlx - dsx * LX) + LX * ((nly - dsy * LY) + LY * (nlz - dsz * LZ));
+            const int destL = s * d.nsc + dest_sc;
+            const int m = warp_aggregated_add(d.mv_count);
+            if (m < d.mv_cap) {
+                d.mv_rank[m] = atomicAdd(d.narrive + destL, 1);
+                d.mv_dest[m] = destL;
+                d.mv_cell[m] = dest_cell;
+                d.mv_ox[m] = nox;
+                d.mv_oy[m] = noy;
+                d.mv_oz[m] = noz;
+                d.mv_ux[m] = ux;
+                d.mv_uy[m] = uy;
+                d.mv_uz[m] = uz;
+                d.mv_w[m] = w;
+                if (d.pid)
+                    d.mv_pid[m] = *pidp;
+            } else {
+                my_status |= ST_CAPACITY;
+            }
         }
         q.cell = -1;
         const int h = atomicAdd(&sh.nholes, 1);

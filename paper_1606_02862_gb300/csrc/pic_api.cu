@@ -93,6 +93,13 @@ struct pic_ctx {
     int4 *blk_sums = nullptr, *blk_offs = nullptr, *totals = nullptr;
     int* work_counter = nullptr;
     int* step_ctr = nullptr;           // device step count, read by the push for its sort passes
+    long long* step_no = nullptr;      // device: steps taken since creation (antenna time)
+    int64_t steps_done = 0;            // host: steps enqueued since creation
+    int* abs_off_d = nullptr;          // [nboxes + 1] block offsets of the y absorber
+    int abs_nblocks = 0;
+    float* shift_scratch = nullptr;    // moving window: copy of one box's field
+    int64_t shift_scratch_floats = 0;
+    int* rot_scratch = nullptr;        // moving window: copies of count, nframes, foff
     int sort_every = kDefaultSortEvery;
     unsigned* wmax_bits = nullptr;     // [kMaxSpecies] device
     float wmax[kMaxSpecies] = {};      // host copy: largest |weight| per species
@@ -340,6 +347,7 @@ StepDev make_step(const pic_ctx* c, int parity)
     d.totals = c->totals;
     d.work_counter = c->work_counter;
     d.step_ctr = c->step_ctr;
+    d.step_no = c->step_no;
     d.sort_every = c->sort_every;
     d.status = c->status_d;
     d.wmax_bits = c->wmax_bits;
@@ -459,7 +467,8 @@ pic_status enqueue_step_mixed(pic_ctx* c, int parity, cudaEvent_t* ev, bool exte
     if (ev)
         CK(record(ev[2], c->stream, external));
     YeePlan yp{c->boxes_d, c->yee_off_d, c->nboxes, c->yee_nblocks, (float)c->dt,
-               {(float)(1.0 / c->h[0]), (float)(1.0 / c->h[1]), (float)(1.0 / c->h[2])}};
+               {(float)(1.0 / c->h[0]), (float)(1.0 / c->h[1]), (float)(1.0 / c->h[2])},
+               c->step_no, c->dt, {c->h[0], c->h[1], c->h[2]}, c->abs_off_d, c->abs_nblocks};
     CK(launch_yee_mixed_plan(yp, c->stream));
     if (ev)
         CK(record(ev[3], c->stream, external));
@@ -695,6 +704,31 @@ int ilog2(int v)
 
 // ============================================================ C ABI
 
+namespace {
+
+// Copy the host box table (open-y options included) to the device and
+// rebuild the absorber's block table; a change of the absorber's launch
+// shape drops the captured graphs.
+pic_status upload_boxes(pic_ctx* c)
+{
+    std::vector<int> off(c->nboxes + 1, 0);
+    for (int b = 0; b < c->nboxes; ++b)
+        off[b + 1] = off[b] + absorber_blocks(c->boxes_h[b]);
+    if (off[c->nboxes] != c->abs_nblocks)
+        destroy_graphs(c);
+    c->abs_nblocks = off[c->nboxes];
+    CK(cudaStreamSynchronize(c->stream));
+    CK(cudaMemcpyAsync(c->boxes_d, c->boxes_h.data(), sizeof(BoxDev) * c->nboxes,
+                       cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->abs_off_d, off.data(), sizeof(int) * (c->nboxes + 1),
+                       cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return PIC_OK;
+}
+
+}  // namespace
+
+
 extern "C" {
 
 pic_status pic_create(const pic_grid* grids, int32_t nboxes, const double dx[3], double dt,
@@ -820,6 +854,8 @@ pic_status pic_create(const pic_grid* grids, int32_t nboxes, const double dx[3],
             bd.nscy = g.ny / c->LY;
             bd.nscz = g.nz / c->LZ;
             bd.sc_base = nsc;
+            bd.oy = OpenYDev{};
+            bd.oy.ant_j = -1;
             nsc += bd.nscx * bd.nscy * bd.nscz;
             floats += 3 * padded_cells(bd);
             yee_off[b + 1] = yee_off[b] + ((g.nx + 31) / 32) * ((g.ny + 7) / 8) * g.nz;
@@ -854,7 +890,8 @@ pic_status pic_create(const pic_grid* grids, int32_t nboxes, const double dx[3],
             dalloc(c, &c->free_top, 1) != PIC_OK || dalloc(c, &c->mv_count, 1) != PIC_OK ||
             dalloc(c, &c->blk_sums, nblk) != PIC_OK || dalloc(c, &c->blk_offs, nblk) != PIC_OK ||
             dalloc(c, &c->totals, 1) != PIC_OK || dalloc(c, &c->work_counter, 1) != PIC_OK ||
-            dalloc(c, &c->step_ctr, 1) != PIC_OK || dalloc(c, &c->wmax_bits, kMaxSpecies) != PIC_OK)
+            dalloc(c, &c->step_ctr, 1) != PIC_OK || dalloc(c, &c->step_no, 1) != PIC_OK ||
+            dalloc(c, &c->abs_off_d, nboxes + 1) != PIC_OK || dalloc(c, &c->wmax_bits, kMaxSpecies) != PIC_OK)
             return bail(PIC_ERR_OOM);
         if (cudaMemcpyAsync(c->boxes_d, c->boxes_h.data(), sizeof(BoxDev) * nboxes,
                             cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
@@ -884,6 +921,108 @@ pic_status pic_set_background(pic_ctx* c, int32_t box, double rho_bg)
         return fail(c, PIC_ERR_ARG, "bad box or background");
     c->rho_bg[box] = rho_bg;
     return PIC_OK;
+}
+
+// ---------------------------------------------------------------- open y
+
+pic_status pic_set_boundary(pic_ctx* c, int32_t box, const pic_boundary* bnd)
+{
+    CKS(check_ctx(c));
+    if (!valid_box(c, box) || !bnd)
+        return fail(c, PIC_ERR_ARG, "bad arguments to pic_set_boundary");
+    if (c->precision != PIC_PRECISION_MIXED)
+        return fail(c, PIC_ERR_ARG, "open y boundaries need the mixed form");
+    BoxDev& b = c->boxes_h[box];
+    if (bnd->absorber_cells < 0 || 2 * (int64_t)bnd->absorber_cells > b.ny ||
+        !(bnd->absorber_sigma >= 0.0) || !std::isfinite(bnd->absorber_sigma))
+        return fail(c, PIC_ERR_ARG, "absorber needs 0 <= 2 cells <= ny and a finite sigma >= 0");
+    b.oy.open_y = bnd->open_y != 0;
+    b.oy.abs_cells = bnd->absorber_cells;
+    b.oy.abs_sigma = (float)bnd->absorber_sigma;
+    return upload_boxes(c);
+}
+
+pic_status pic_set_antenna(pic_ctx* c, int32_t box, const pic_antenna* a)
+{
+    CKS(check_ctx(c));
+    if (!valid_box(c, box) || !a)
+        return fail(c, PIC_ERR_ARG, "bad arguments to pic_set_antenna");
+    if (c->precision != PIC_PRECISION_MIXED)
+        return fail(c, PIC_ERR_ARG, "the antenna needs the mixed form");
+    BoxDev& b = c->boxes_h[box];
+    if (a->plane_y < 0) {
+        b.oy.ant_j = -1;
+        return upload_boxes(c);
+    }
+    const double vals[7] = {a->E0, a->omega, a->w0, a->xc, a->zc, a->tau, a->t0};
+    for (double v : vals)
+        if (!std::isfinite(v))
+            return fail(c, PIC_ERR_ARG, "non-finite antenna parameter");
+    // Yee dispersion along y: sin(kappa/2) = (dy/dt) sin(omega dt/2)
+    const double sk = (c->h[1] / c->dt) * std::sin(0.5 * a->omega * c->dt);
+    if (a->plane_y >= b.ny || !(std::fabs(sk) < 1.0))
+        return fail(c, PIC_ERR_ARG, "antenna plane outside the box or omega not resolved by the grid");
+    const double kappa = 2.0 * std::asin(sk);
+    b.oy.ant_j = a->plane_y;
+    b.oy.ant_J0 = -2.0 * a->E0 * std::cos(0.5 * kappa) / c->h[1];
+    b.oy.ant_omega = a->omega;
+    b.oy.ant_w0 = a->w0;
+    b.oy.ant_xc = a->xc;
+    b.oy.ant_zc = a->zc;
+    b.oy.ant_tau = a->tau;
+    b.oy.ant_t0 = a->t0;
+    return upload_boxes(c);
+}
+
+pic_status pic_shift_window(pic_ctx* c, int32_t box, int32_t cells)
+{
+    CKS(check_ctx(c));
+    if (!valid_box(c, box))
+        return fail(c, PIC_ERR_ARG, "bad box");
+    if (c->precision != PIC_PRECISION_MIXED)
+        return fail(c, PIC_ERR_ARG, "the moving window needs the mixed form");
+    const BoxDev& b = c->boxes_h[box];
+    if (cells <= 0 || cells >= b.ny || cells % c->LY)
+        return fail(c, PIC_ERR_ARG, "shift must be a positive multiple of the supercell edge along y, below ny");
+    const int rows = cells / c->LY;
+    CK(cudaStreamSynchronize(c->stream));
+    // fields: E and B through a copy of the box's field
+    const int64_t pf = 3 * padded_cells(b);
+    if (c->shift_scratch_floats < pf) {
+        raw_free(c, c->shift_scratch);
+        c->shift_scratch = nullptr;
+        c->shift_scratch_floats = 0;
+        CKS(dalloc(c, &c->shift_scratch, pf, false));
+        c->shift_scratch_floats = pf;
+    }
+    for (float* F : {b.E, b.B}) {
+        CK(cudaMemcpyAsync(c->shift_scratch, F, sizeof(float) * pf, cudaMemcpyDeviceToDevice, c->stream));
+        CK(launch_shift_fields(b, F, c->shift_scratch, cells, c->stream));
+    }
+    CK(cudaMemsetAsync(b.J, 0, sizeof(float) * pf, c->stream));
+    // particles: empty the bottom rows, release their frames through one
+    // maintenance pass, then rotate the box's lists down by `rows`
+    StepDev d = make_step(c, c->parity);
+    d.step_ctr = nullptr;
+    CK(launch_clear_rows(d, b, rows, c->stream));
+    CK(cudaMemsetAsync(c->mv_count, 0, sizeof(int), c->stream));
+    CK(launch_frame_plan(d, c->stream));
+    CK(launch_frame_apply(d, 4 * c->nsm, c->stream));
+    CKS(status_check(c));
+    c->parity ^= 1;
+    if (!c->rot_scratch)
+        CKS(dalloc(c, &c->rot_scratch, 3 * (int64_t)c->nlists, false));
+    CK(cudaMemcpyAsync(c->rot_scratch, c->count, sizeof(int) * c->nlists, cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->rot_scratch + c->nlists, c->nframes, sizeof(int) * c->nlists,
+                       cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->rot_scratch + 2 * c->nlists, c->foff[c->parity], sizeof(int) * c->nlists,
+                       cudaMemcpyDeviceToDevice, c->stream));
+    d = make_step(c, c->parity);
+    CK(launch_rotate_lists(d, b, c->rot_scratch, c->foff[c->parity], rows, c->stream));
+    // a shift by whole supercells keeps every particle's cell and its list
+    // order: nothing else to redo
+    CK(cudaStreamSynchronize(c->stream));
+    return status_check(c);
 }
 
 pic_status pic_load_particles(pic_ctx* c, int32_t box, int32_t species, int64_t n,
@@ -1007,6 +1146,7 @@ pic_status pic_step_async(pic_ctx* c, int32_t nsteps)
             if (c->timing)
                 CKS(step_events(c, &ev));
             CKS(enqueue_step_plain(c, ev));
+            ++c->steps_done;
         }
         return PIC_OK;
     }
@@ -1022,6 +1162,7 @@ pic_status pic_step_async(pic_ctx* c, int32_t nsteps)
         else
             CKS(enqueue_step_mixed(c, c->parity, ev));
         c->parity ^= 1;
+        ++c->steps_done;
     }
     return PIC_OK;
 }
@@ -1222,7 +1363,8 @@ pic_status pic_info(pic_ctx* c, int32_t key, int64_t* out)
         return PIC_OK;
     case PIC_INFO_KERNELS_PER_STEP:
         if (c->precision == PIC_PRECISION_MIXED) {
-            *out = 1 + 2 + 3 + 3;  // push; scan reduce, top; apply, place, free; Yee x3
+            // push; scan reduce, top; apply, place, free; Yee x3; y absorber
+            *out = 1 + 2 + 3 + 3 + (c->abs_nblocks > 0 ? 1 : 0);
         } else {
             int64_t k = 0;
             for (int b = 0; b < c->nboxes; ++b) {
@@ -1246,6 +1388,9 @@ pic_status pic_info(pic_ctx* c, int32_t key, int64_t* out)
         *out = c->pool_cap - top;
         return PIC_OK;
     }
+    case PIC_INFO_STEPS:
+        *out = c->steps_done;
+        return PIC_OK;
     case PIC_INFO_MOVE_CAPACITY:
         *out = c->mv_cap;
         return PIC_OK;

@@ -53,6 +53,15 @@ struct SpeciesDev {
     int pad;
 };
 
+// Open-y options of a box (pic_set_boundary, pic_set_antenna).
+struct OpenYDev {
+    int open_y;               // particles leaving through a y face are removed
+    int abs_cells;            // damping layer thickness at both y faces (0: none)
+    float abs_sigma;          // damping factor exp(-sigma d^2) per step
+    int ant_j;                // antenna node plane (-1: none)
+    double ant_J0, ant_omega, ant_w0, ant_xc, ant_zc, ant_tau, ant_t0;
+};
+
 struct BoxDev {
     int nx, ny, nz;
     int px, py, pz;           // padded extents
@@ -61,6 +70,7 @@ struct BoxDev {
     float* E;                 // 3 * px*py*pz, component-major
     float* B;
     float* J;
+    OpenYDev oy;
 };
 
 // Everything the mixed-form step kernels need, passed by value.
@@ -118,6 +128,7 @@ struct StepDev {
     int4* totals;             // device scalar: frames, alloc, release, -
     int* work_counter;        // persistent-kernel work counter
     int* step_ctr;            // device step count (advanced by the frame plan)
+    long long* step_no;       // steps taken since creation (advanced with step_ctr, never reset)
     int sort_every;           // the push sorts the frame lists every this many steps
     unsigned* status;         // device status word
     unsigned* wmax_bits;      // [kMaxSpecies] float bits of the largest |weight| loaded
@@ -146,6 +157,11 @@ struct YeePlan {
     int nblocks;
     float dt;
     float ih[3];
+    const long long* step_no;  // steps taken, incremented before the field update of a step
+    double dt_d;               // dt in FP64 (antenna time)
+    double dx_d[3];            // cell edges in FP64 (antenna profile)
+    const int* abs_off;        // device [nboxes + 1] block offsets of the y absorber (or null)
+    int abs_nblocks;
 };
 cudaError_t configure_push(int LX, int LY, int LZ, int threads, int* per_sm);
 cudaError_t launch_push_deposit(const StepDev& d, int threads, int grid, cudaStream_t st);
@@ -161,6 +177,12 @@ cudaError_t launch_read_particles(const StepDev& d, const BoxDev& hb, int box, i
                                   const int* list_off, double* x, double* u, double* w,
                                   int64_t* id, cudaStream_t st);
 cudaError_t launch_yee_mixed_plan(const YeePlan& p, cudaStream_t st);
+int absorber_blocks(const BoxDev& b);
+cudaError_t launch_shift_fields(const BoxDev& b, float* F, const float* scratch, int cells,
+                                cudaStream_t st);
+cudaError_t launch_clear_rows(const StepDev& d, const BoxDev& hb, int rows, cudaStream_t st);
+cudaError_t launch_rotate_lists(const StepDev& d, const BoxDev& hb, const int* old3, int* foff,
+                                int rows, cudaStream_t st);
 cudaError_t launch_fields_to_padded(const BoxDev& b, int which, const double* src,
                                     cudaStream_t st);
 cudaError_t launch_fields_from_padded(const BoxDev& b, int which, double* dst, cudaStream_t st);

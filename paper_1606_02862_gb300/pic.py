@@ -29,11 +29,13 @@ PRECISION_MIXED = 1
 FIELD_E, FIELD_B, FIELD_J, FIELD_RHO = 0, 1, 2, 3
 
 # every symbol include/pic.h declares
-EXPORTED = ("pic_create", "pic_set_background", "pic_load_particles", "pic_write_fields",
+EXPORTED = ("pic_create", "pic_set_background", "pic_set_boundary", "pic_set_antenna",
+            "pic_shift_window", "pic_load_particles", "pic_write_fields",
             "pic_step", "pic_step_async", "pic_sync", "pic_read_fields", "pic_count_particles",
             "pic_read_particles", "pic_diagnostics", "pic_stage_timing", "pic_stage_times",
             "pic_info", "pic_field_energy_noalloc", "pic_last_error", "pic_destroy")
-INFO_GRAPH_ACTIVE, INFO_KERNELS_PER_STEP, INFO_POOL_FRAMES, INFO_FRAMES_USED, INFO_MOVE_CAPACITY = range(5)
+(INFO_GRAPH_ACTIVE, INFO_KERNELS_PER_STEP, INFO_POOL_FRAMES, INFO_FRAMES_USED, INFO_MOVE_CAPACITY,
+ INFO_STEPS) = range(6)
 
 
 class PicError(RuntimeError):
@@ -49,6 +51,16 @@ class Grid(ctypes.Structure):
 class SpeciesC(ctypes.Structure):
     _fields_ = [("charge", ctypes.c_double), ("mass", ctypes.c_double),
                 ("shape", ctypes.c_int32), ("mobile", ctypes.c_int32)]
+
+
+class Boundary(ctypes.Structure):
+    _fields_ = [("open_y", ctypes.c_int32), ("absorber_cells", ctypes.c_int32),
+                ("absorber_sigma", ctypes.c_double)]
+
+
+class AntennaC(ctypes.Structure):
+    _fields_ = [("plane_y", ctypes.c_int32), ("reserved", ctypes.c_int32)] + \
+        [(k, ctypes.c_double) for k in ("E0", "omega", "w0", "xc", "zc", "tau", "t0")]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
@@ -81,6 +93,9 @@ def library(path: str = LIB_PATH):
                              ctypes.c_double, ctypes.POINTER(SpeciesC), i32,
                              ctypes.POINTER(Options), ctypes.POINTER(vp)]
     L.pic_set_background.argtypes = [vp, i32, ctypes.c_double]
+    L.pic_set_boundary.argtypes = [vp, i32, ctypes.POINTER(Boundary)]
+    L.pic_set_antenna.argtypes = [vp, i32, ctypes.POINTER(AntennaC)]
+    L.pic_shift_window.argtypes = [vp, i32, i32]
     L.pic_load_particles.argtypes = [vp, i32, i32, i64, dp, dp, dp]
     L.pic_write_fields.argtypes = [vp, i32, i32, dp]
     L.pic_step.argtypes = [vp, i32]
@@ -204,6 +219,25 @@ class Context:
     # ------------------------------------------------------------ ABI calls
     def set_background(self, box, rho_bg):
         self._check(self._L.pic_set_background(self._ctx, box, float(rho_bg)))
+
+    def set_boundary(self, box, open_y=False, absorber_cells=0, absorber_sigma=0.0):
+        """Open y faces: remove particles leaving through them, and/or damping
+        layers of absorber_cells cells (factor exp(-sigma d^2) per step)."""
+        b = Boundary(int(bool(open_y)), int(absorber_cells), float(absorber_sigma))
+        self._check(self._L.pic_set_boundary(self._ctx, box, ctypes.byref(b)))
+
+    def set_antenna(self, box, plane_y, E0=0.0, omega=0.0, w0=0.0, xc=0.0, zc=0.0, tau=0.0, t0=0.0):
+        """Ex current-sheet laser antenna on the node plane y = plane_y (< 0: none)."""
+        a = AntennaC(int(plane_y), 0, float(E0), float(omega), float(w0), float(xc), float(zc),
+                     float(tau), float(t0))
+        self._check(self._L.pic_set_antenna(self._ctx, box, ctypes.byref(a)))
+
+    def shift_window(self, box, cells):
+        """Moving window: box moves `cells` (a multiple of the supercell edge) towards +y."""
+        self._check(self._L.pic_shift_window(self._ctx, box, int(cells)))
+
+    def steps_taken(self):
+        return self.info(INFO_STEPS)
 
     def load_particles(self, box, species, x, u, w=None):
         x = _f64(x, (-1, 3))

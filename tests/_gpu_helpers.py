@@ -21,9 +21,10 @@ def ctx_from(wl, **kw):
     return pic.from_workload(wl, **kw)
 
 
-def oracle_state_from_gpu(orc, ctx, wl, box):
+def oracle_state_from_gpu(orc, ctx, wl, box, **state_kw):
     """The GPU's current state of one box, read back in FP64, as an oracle
-    State (particles of each species sorted by id)."""
+    State (particles of each species sorted by id, the ids attached to the
+    oracle species as `ids`).  state_kw go to the State (open-y options, t)."""
     from paper_1606_02862_gb300 import pic
 
     b = wl.boxes[box]
@@ -35,9 +36,12 @@ def oracle_state_from_gpu(orc, ctx, wl, box):
         p = ctx.read_particles(box, si, ids=True)
         order = np.argsort(p["id"])
         ids.append(p["id"][order])
-        species.append(orc.Species(q=sd.q, m=sd.m, order=sd.shape, x=p["x"][order], u=p["u"][order],
-                                   w=p["w"][order], mobile=sd.mobile))
-    st = orc.State(b.nx, b.ny, b.nz, wl.dt, dx=wl.dx, E=E, B=B, species=species, rho_bg=b.rho_bg)
+        osp = orc.Species(q=sd.q, m=sd.m, order=sd.shape, x=p["x"][order], u=p["u"][order],
+                          w=p["w"][order], mobile=sd.mobile)
+        osp.ids = p["id"][order]
+        species.append(osp)
+    st = orc.State(b.nx, b.ny, b.nz, wl.dt, dx=wl.dx, E=E, B=B, species=species, rho_bg=b.rho_bg,
+                   **state_kw)
     return st, ids
 
 
