@@ -455,6 +455,9 @@ WORKLOADS = {
     "laser_ramp": "128x1024x128, e- + p+ 4 ppc each in a density ramp to 0.01 n_c, Gaussian pulse a0 3",
     "foil_overdense": "256x2048x256, 20-cell foil of e- + C6+ at 30 n_c, 16 ppc each, Gaussian pulse a0 10",
     "khi_128": "128^3, e- + p+ 16 ppc each, shear slabs at +-0.2c, TSC (the paper's evaluation size)",
+    "laser_window": "128x1024x128, e- + p+ 4 ppc each in a density ramp to 0.01 n_c; open y: 32-cell "
+                    "absorbers, particles leaving through y removed, antenna-injected pulse a0 3, moving "
+                    "window advanced by 4 cells whenever c t passes them, fresh plasma loaded at the top",
 }
 
 
@@ -514,6 +517,81 @@ def run_workload(args):
                if plain else {})}
 
 
+def run_window(args):
+    """The open-boundary laser workload with a moving window: push+deposit
+    rate from the in-graph stage events (steps only), and the whole cycle per
+    step including the window shifts and the loading of fresh plasma, timed
+    with CUDA events around the loop (slabs generated before the timed region)."""
+    import torch
+
+    from paper_1606_02862_gb300 import build as libbuild
+    from paper_1606_02862_gb300 import pic
+    from paper_1606_02862_gb300 import workloads as W
+
+    libbuild.build()
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    t0 = time.perf_counter()
+    wl = W.laser_window()
+    b = wl.boxes[0]
+    log(f"generated laser_window in {time.perf_counter() - t0:.1f} s")
+    sc = (8, 4, 4) if args.sc == "auto" else tuple(int(v) for v in args.sc.split("x"))
+    threads = args.threads or 256
+    ctx = pic.from_workload(wl, sc=sc, threads_per_sc=threads)
+    step_cells = sc[1]
+    rng = np.random.default_rng(wl.extra["seed"] + 1)
+    total = args.warmup + args.steps
+    nshift = int(total * wl.dt / step_cells) + 1
+    slabs = [W.window_slab(rng, b.nx, b.nz, b.ny - step_cells, b.ny, wl.extra["ppc"], wl.extra["density"],
+                           y_shift=float((k + 1) * step_cells)) for k in range(nshift)]
+    state = {"shifts": 0}
+
+    def advance(k):
+        ctx.step_async(1)
+        if (k + 1) * wl.dt >= (state["shifts"] + 1) * step_cells:
+            ctx.shift_window(0, step_cells)
+            for si, (x, u, w) in enumerate(slabs[state["shifts"]]):
+                ctx.load_particles(0, si, x, u, w)
+            state["shifts"] += 1
+
+    for k in range(args.warmup):
+        advance(k)
+    ctx.sync()
+    npart = sum(ctx.count_particles(0, s) for s in range(2))
+    shifts0 = state["shifts"]
+    ctx.stage_timing(True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(args.warmup, total):
+        advance(k)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    cycle_ms = e0.elapsed_time(e1) / args.steps
+    ms, nst = ctx.stage_times()
+    npart1 = sum(ctx.count_particles(0, s) for s in range(2))
+    ctx.close()
+    del wl, slabs
+    npart_avg = 0.5 * (npart + npart1)
+    pd = (ms[0] + ms[1]) / nst
+    hbm, hbm_src = measured_hbm()
+    achieved = (npart_avg * MIXED_BYTES_PER_PARTICLE + b.ncells * MIXED_BYTES_PER_CELL) / (ms[0] / nst * 1e-3) / 1e9
+    return {"metric": METRIC, "value": npart_avg / (pd * 1e-3), "unit": UNIT, "n_gpus": 1,
+            "steps": nst, "warmup": args.warmup, "ms_per_step": ms[3] / nst, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"laser_window: {WORKLOADS['laser_window']} (~{int(npart_avg)} particles, "
+                                   f"{b.ncells} cells)",
+                       "form": f"mixed, supercell {'x'.join(map(str, sc))}, {threads} threads"},
+            "stage_ms_per_step": {"push_deposit_kernel": ms[0] / nst, "frame_maintenance": ms[1] / nst,
+                                  "yee_and_absorber": ms[2] / nst},
+            "window": {"shifts": state["shifts"] - shifts0, "cycle_ms_per_step": cycle_ms,
+                       "what": "CUDA events around the loop: steps, window shifts and fresh-plasma loads "
+                               "from host FP64 arrays"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm, "traffic": None, "kernel": "k_push_deposit",
+                         "peak_source": hbm_src}}
+
+
 # ----------------------------------------------------------------------------- reference arm
 
 def run_reference(args, rank):
@@ -564,7 +642,7 @@ def main():
                     help="particle shape of the headline thermal workload")
     ap.add_argument("--workload", default="thermal_tsc_256",
                     choices=["thermal_tsc_256", "small_cic_32", "laser_ramp", "foil_overdense",
-                             "khi_128"])
+                             "khi_128", "laser_window"])
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -578,6 +656,8 @@ def main():
         dist = dist_mod
     if args.impl == "reference":
         line = run_reference(args, rank)
+    elif args.workload == "laser_window":
+        line = run_window(args) if rank == 0 else None
     elif args.workload != "thermal_tsc_256":
         line = run_workload(args) if rank == 0 else None
     else:

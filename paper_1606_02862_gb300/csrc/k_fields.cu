@@ -51,10 +51,11 @@ struct CellAt {
     bool ok;
 };
 
-__device__ __forceinline__ CellAt yee_cell(const YeeArgs& a, BoxDev& b)
+__device__ __forceinline__ CellAt yee_cell(const YeeArgs& a, const BoxDev*& bp)
 {
     const int box = find_box(a.blk_off, a.nboxes, blockIdx.x);
-    b = a.boxes[box];
+    bp = a.boxes + box;  // fields read through the pointer as used, not copied
+    const BoxDev& b = *bp;
     const int local = blockIdx.x - a.blk_off[box];
     const int nbx = (b.nx + 31) >> 5, nby = (b.ny + 7) >> 3;
     CellAt c;
@@ -94,10 +95,11 @@ __device__ __forceinline__ void store_with_images(const BoxDev& b, float* F, con
 
 __global__ void __launch_bounds__(256) k_yee_b(const YeeArgs a)
 {
-    BoxDev b;
-    CellAt c = yee_cell(a, b);
+    const BoxDev* bp;
+    CellAt c = yee_cell(a, bp);
     if (!c.ok)
         return;
+    const BoxDev& b = *bp;
     const int64_t pc = padded_cells(b);
     const int64_t sx = 1, sy = b.px, sz = (int64_t)b.px * b.py;
     const int64_t i = padded_index(b, c.x, c.y, c.z);
@@ -112,10 +114,12 @@ __global__ void __launch_bounds__(256) k_yee_b(const YeeArgs a)
     store_with_images(b, Bz, c, Bz[i] - a.tau * cz);
 }
 
-// Laser antenna: the sheet current at the Ex position (x+1/2, ant_j, z) at
-// the time of this step's current, t = (n + 1/2) dt, n = steps taken before
-// it (step_no was advanced earlier in the step).  FP64 throughout: omega t
-// reaches thousands of radians.
+// Laser antenna: adds the sheet current at the Ex positions
+// (x+1/2, ant_j, z) of every box with an antenna into J, at the time of this
+// step's current, t = (n + 1/2) dt, n = steps taken before it (step_no was
+// advanced earlier in the step).  Runs before the E update, which folds it
+// in with the deposits.  FP64 throughout: omega t reaches thousands of
+// radians.  One thread per (box, x, z), grid-stride.
 __device__ __forceinline__ float antenna_current(const YeeArgs& a, const BoxDev& b, int x, int z)
 {
     const OpenYDev& o = b.oy;
@@ -130,12 +134,29 @@ __device__ __forceinline__ float antenna_current(const YeeArgs& a, const BoxDev&
     return (float)(o.ant_J0 * G * T * cos(o.ant_omega * (t - o.ant_t0)));
 }
 
+__global__ void __launch_bounds__(256) k_antenna(const YeeArgs a)
+{
+    for (int box = 0; box < a.nboxes; ++box) {
+        const BoxDev& b = a.boxes[box];
+        const int j = b.oy.ant_j;
+        if (j < 0)
+            continue;
+        const int64_t n = (int64_t)b.nx * b.nz;
+        for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
+             t += (int64_t)gridDim.x * blockDim.x) {
+            const int x = (int)(t % b.nx), z = (int)(t / b.nx);
+            b.J[padded_index(b, x, j, z)] += antenna_current(a, b, x, z);
+        }
+    }
+}
+
 __global__ void __launch_bounds__(256) k_yee_e(const YeeArgs a)
 {
-    BoxDev b;
-    CellAt c = yee_cell(a, b);
+    const BoxDev* bp;
+    CellAt c = yee_cell(a, bp);
     if (!c.ok)
         return;
+    const BoxDev& b = *bp;
     const int64_t pc = padded_cells(b);
     const int64_t sx = 1, sy = b.px, sz = (int64_t)b.px * b.py;
     const int64_t i = padded_index(b, c.x, c.y, c.z);
@@ -156,8 +177,6 @@ __global__ void __launch_bounds__(256) k_yee_e(const YeeArgs a)
                     b.J[2 * pc + g] = 0.f;
                 }
             }
-    if (c.y == b.oy.ant_j)
-        jx += antenna_current(a, b, c.x, c.z);
     b.J[i] = jx;
     b.J[pc + i] = jy;
     b.J[2 * pc + i] = jz;
@@ -199,7 +218,7 @@ int absorber_blocks(const BoxDev& b)
 __global__ void __launch_bounds__(256) k_absorb_y(const BoxDev* boxes, const int* off, int nboxes)
 {
     const int box = find_box(off, nboxes, blockIdx.x);
-    const BoxDev b = boxes[box];
+    const BoxDev& b = boxes[box];
     const int A = b.oy.abs_cells;
     const int64_t t = (int64_t)(blockIdx.x - off[box]) * 256 + threadIdx.x;
     if (A <= 0 || t >= (int64_t)2 * A * b.nx * b.nz)
@@ -229,6 +248,8 @@ cudaError_t launch_yee_mixed_plan(const YeePlan& p, cudaStream_t st)
               p.step_no, p.dt_d, {p.dx_d[0], p.dx_d[1], p.dx_d[2]}};
     dim3 blk(32, 8);
     k_yee_b<<<p.nblocks, blk, 0, st>>>(a);
+    if (p.antenna)
+        k_antenna<<<64, 256, 0, st>>>(a);
     a.tau = p.dt;
     k_yee_e<<<p.nblocks, blk, 0, st>>>(a);
     a.tau = 0.5f * p.dt;

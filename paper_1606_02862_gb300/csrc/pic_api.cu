@@ -97,6 +97,7 @@ struct pic_ctx {
     int64_t steps_done = 0;            // host: steps enqueued since creation
     int* abs_off_d = nullptr;          // [nboxes + 1] block offsets of the y absorber
     int abs_nblocks = 0;
+    bool any_antenna = false;
     float* shift_scratch = nullptr;    // moving window: copy of one box's field
     int64_t shift_scratch_floats = 0;
     int* rot_scratch = nullptr;        // moving window: copies of count, nframes, foff
@@ -468,7 +469,8 @@ pic_status enqueue_step_mixed(pic_ctx* c, int parity, cudaEvent_t* ev, bool exte
         CK(record(ev[2], c->stream, external));
     YeePlan yp{c->boxes_d, c->yee_off_d, c->nboxes, c->yee_nblocks, (float)c->dt,
                {(float)(1.0 / c->h[0]), (float)(1.0 / c->h[1]), (float)(1.0 / c->h[2])},
-               c->step_no, c->dt, {c->h[0], c->h[1], c->h[2]}, c->abs_off_d, c->abs_nblocks};
+               c->step_no, c->dt, {c->h[0], c->h[1], c->h[2]}, c->abs_off_d, c->abs_nblocks,
+               c->any_antenna ? 1 : 0};
     CK(launch_yee_mixed_plan(yp, c->stream));
     if (ev)
         CK(record(ev[3], c->stream, external));
@@ -714,9 +716,13 @@ pic_status upload_boxes(pic_ctx* c)
     std::vector<int> off(c->nboxes + 1, 0);
     for (int b = 0; b < c->nboxes; ++b)
         off[b + 1] = off[b] + absorber_blocks(c->boxes_h[b]);
-    if (off[c->nboxes] != c->abs_nblocks)
+    bool ant = false;
+    for (int b = 0; b < c->nboxes; ++b)
+        ant = ant || c->boxes_h[b].oy.ant_j >= 0;
+    if (off[c->nboxes] != c->abs_nblocks || ant != c->any_antenna)
         destroy_graphs(c);
     c->abs_nblocks = off[c->nboxes];
+    c->any_antenna = ant;
     CK(cudaStreamSynchronize(c->stream));
     CK(cudaMemcpyAsync(c->boxes_d, c->boxes_h.data(), sizeof(BoxDev) * c->nboxes,
                        cudaMemcpyHostToDevice, c->stream));
@@ -1037,7 +1043,8 @@ pic_status pic_load_particles(pic_ctx* c, int32_t box, int32_t species, int64_t 
     int64_t& idn = c->id_next[(size_t)box * c->sp.size() + species];
     if (idn + n > INT32_MAX)
         return fail(c, PIC_ERR_ARG, "more than 2^31 particles in one (box, species)");
-    destroy_graphs(c);
+    // captured step graphs stay valid unless a buffer they use is reallocated
+    // (ensure_pool / ensure_mv drop them) or a weight bound grows (below)
     const int64_t chunk = std::min<int64_t>(n, 1 << 22);
     CKS(ensure_stage(c, sizeof(double) * 7 * (size_t)chunk));
     double* sx = static_cast<double*>(c->stage_d);
@@ -1363,8 +1370,8 @@ pic_status pic_info(pic_ctx* c, int32_t key, int64_t* out)
         return PIC_OK;
     case PIC_INFO_KERNELS_PER_STEP:
         if (c->precision == PIC_PRECISION_MIXED) {
-            // push; scan reduce, top; apply, place, free; Yee x3; y absorber
-            *out = 1 + 2 + 3 + 3 + (c->abs_nblocks > 0 ? 1 : 0);
+            // push; scan reduce, top; apply, place, free; Yee x3; antenna; y absorber
+            *out = 1 + 2 + 3 + 3 + (c->any_antenna ? 1 : 0) + (c->abs_nblocks > 0 ? 1 : 0);
         } else {
             int64_t k = 0;
             for (int b = 0; b < c->nboxes; ++b) {

@@ -162,6 +162,7 @@ struct YeePlan {
     double dx_d[3];            // cell edges in FP64 (antenna profile)
     const int* abs_off;        // device [nboxes + 1] block offsets of the y absorber (or null)
     int abs_nblocks;
+    int antenna;               // nonzero: some box has an antenna (launch k_antenna)
 };
 cudaError_t configure_push(int LX, int LY, int LZ, int threads, int* per_sm);
 cudaError_t launch_push_deposit(const StepDev& d, int threads, int grid, cudaStream_t st);

@@ -367,6 +367,11 @@ def from_workload(wl, precision=PRECISION_MIXED, sc=(4, 4, 4), threads_per_sc=0,
                   [Species(s.q, s.m, s.shape, s.mobile) for s in wl.species], precision=precision,
                   sc=sc, threads_per_sc=threads_per_sc, track_ids=track_ids, use_graph=use_graph,
                   **kw)
+    extra = getattr(wl, "extra", None) or {}
+    if "boundary" in extra:
+        ctx.set_boundary(0, **extra["boundary"])
+    if "antenna" in extra:
+        ctx.set_antenna(0, **extra["antenna"])
     for bi, b in enumerate(wl.boxes):
         ctx.set_background(bi, b.rho_bg)
         for si, (x, u, w) in enumerate(b.particles):

@@ -77,6 +77,7 @@ class Workload:
     dx: tuple = (1.0, 1.0, 1.0)
     steps: int = 1
     note: str = ""
+    extra: dict = field(default_factory=dict)  # open-y options of the first box, window recipe
 
     @property
     def nparticles(self) -> int:
@@ -237,6 +238,56 @@ def laser_ramp(nx=128, ny=1024, nz=128, ppc=4, seed_offset=2, lam=32.0, a0=3.0, 
                   E=E, B=B)
     sp = [SpeciesDef("e", -1.0, 1.0, 2), SpeciesDef("p", 1.0, PROTON_MASS, 2)]
     return Workload("laser_ramp", DT_HALF_COURANT, sp, [box], steps=1000)
+
+
+def window_slab(rng, nx, nz, y0, y1, ppc, density, u_th=0.001, species_masses=(1.0, PROTON_MASS),
+                y_shift=0.0):
+    """Fresh plasma for rows y0 <= y < y1 of a moving window: for each species
+    (masses in m_e), ppc particles per cell, weights following density(y) at
+    each cell row's centre (y in the lab frame, y_shift + box y), thermal
+    momenta u_th / sqrt(m).  Returns [(x, u, w), ...] in box coordinates."""
+    out = []
+    for m in species_masses:
+        x = uniform_in_cells(rng, nx, y1 - y0, nz, ppc) + np.array([0.0, float(y0), 0.0])
+        row = np.floor(x[:, 1]) + 0.5 + y_shift
+        w = density(row) / ppc
+        keep = w > 0.0
+        x, w = x[keep], w[keep]
+        out.append((x, maxwellian(rng, x.shape[0], u_th / math.sqrt(m)), w))
+    return out
+
+
+def laser_window(nx=128, ny=1024, nz=128, ppc=4, seed_offset=5, lam=32.0, a0=3.0, waist=16.0,
+                 duration=40.0, ramp=(160, 360), n_frac=0.01, absorber=32, sigma=1.0,
+                 antenna_y=40) -> Workload:
+    """The laser-ramp setup with open y boundaries: damping layers of
+    `absorber` cells at both y faces, particles leaving through them removed,
+    the pulse injected by an antenna on the plane y = antenna_y (amplitude
+    a0 omega, 1/e radius waist, 1/e half duration `duration`, peak at 2
+    durations), and a moving window that the caller advances by whole
+    supercell rows, loading fresh plasma (window_slab) at the top.  e- + p+
+    at ppc each in a density rising linearly from 0 at y = ramp[0] to n_frac
+    n_c at ramp[1], flat beyond."""
+    rng = np.random.default_rng(BASE_SEED + seed_offset)
+    omega = 2.0 * math.pi / lam
+    n0 = n_frac * omega ** 2
+
+    def density(y):
+        return n0 * np.clip((np.asarray(y) - ramp[0]) / (ramp[1] - ramp[0]), 0.0, 1.0)
+
+    parts = window_slab(rng, nx, nz, 0, ny, ppc, density)
+    box = BoxInit(nx, ny, nz, particles=parts)
+    sp = [SpeciesDef("e", -1.0, 1.0, 2), SpeciesDef("p", 1.0, PROTON_MASS, 2)]
+    wl = Workload("laser_window", DT_HALF_COURANT, sp, [box], steps=1000)
+    wl.extra = {
+        "boundary": dict(open_y=True, absorber_cells=absorber, absorber_sigma=sigma),
+        "antenna": dict(plane_y=antenna_y, E0=a0 * omega, omega=omega, w0=waist, xc=nx / 2.0,
+                        zc=nz / 2.0, tau=duration, t0=2.0 * duration),
+        "density": density,
+        "ppc": ppc,
+        "seed": BASE_SEED + seed_offset,
+    }
+    return wl
 
 
 def iter_batched_uneven(nboxes=64, seed_offset=3, sizes=tuple(range(16, 97, 8)), max_ppc=16,

@@ -185,3 +185,57 @@ def test_open_y_rejected_in_plain_form():
             ctx.set_antenna(0, plane_y=2, E0=1.0, omega=0.5)
     finally:
         ctx.close()
+
+
+def test_laser_window_run_matches_oracle(orc):
+    """The open-boundary laser workload at reduced size through 70 steps with
+    the window advanced by 4 cells whenever c t passes them (5 shifts) and the
+    same fresh plasma loaded on both sides: particle counts, charge, field
+    energy and E against the oracle run of the same recipe."""
+    from paper_1606_02862_gb300 import pic
+    from paper_1606_02862_gb300 import workloads as W
+
+    require_gpu()
+    wl = W.laser_window(nx=16, ny=96, nz=16, ppc=2, lam=16.0, a0=0.5, waist=6.0, duration=10.0,
+                        ramp=(40, 70), absorber=12, antenna_y=16)
+    b = wl.boxes[0]
+    ctx = ctx_from(wl, sc=(8, 4, 4), threads_per_sc=256)
+    a = wl.extra["antenna"]
+    bd = wl.extra["boundary"]
+    species = []
+    for sd, (x, u, w) in zip(wl.species, b.particles):
+        species.append(orc.Species(sd.q, sd.m, sd.shape, x, u, w))
+    st = orc.State(b.nx, b.ny, b.nz, wl.dt, species=species, open_y=True,
+                   absorber=(bd["absorber_cells"], bd["absorber_sigma"]),
+                   antenna=orc.Antenna(ja=a["plane_y"], E0=a["E0"], omega=a["omega"], w0=a["w0"],
+                                       xc=a["xc"], zc=a["zc"], tau=a["tau"], t0=a["t0"]))
+    rng = np.random.default_rng(77)
+    shifts = 0
+    try:
+        for k in range(70):
+            ctx.step(1)
+            st.step(1)
+            if (k + 1) * wl.dt >= (shifts + 1) * 4:
+                shifts += 1
+                ctx.shift_window(0, 4)
+                st.shift_window(4)
+                slab = W.window_slab(rng, b.nx, b.nz, b.ny - 4, b.ny, 2, wl.extra["density"],
+                                     y_shift=float(4 * shifts))
+                for si, (x, u, w) in enumerate(slab):
+                    ctx.load_particles(0, si, x, u, w)
+                    sp = st.species[si]
+                    sp.x = np.vstack([sp.x, x])
+                    sp.u = np.vstack([sp.u, u])
+                    sp.w = np.concatenate([sp.w, w])
+        assert shifts == 5
+        for si in range(2):
+            n_gpu, n_orc = ctx.count_particles(0, si), st.species[si].x.shape[0]
+            assert abs(n_gpu - n_orc) <= 2, (si, n_gpu, n_orc)
+        d_gpu, d_orc = ctx.diagnostics(0), st.diagnostics()
+        print("laser window run: gpu", d_gpu, "oracle", d_orc)
+        assert abs(d_gpu[0] / d_orc[0] - 1) < 1e-3
+        assert abs(d_gpu[2] - d_orc[2]) < 1e-6 * max(1.0, abs(d_orc[2])) + 2 * 0.01
+        E = ctx.read_fields(0, pic.FIELD_E)
+        assert np.max(np.abs(E - st.E)) < 1e-3 * np.max(np.abs(st.E))
+    finally:
+        ctx.close()
