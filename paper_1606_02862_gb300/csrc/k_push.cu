@@ -300,6 +300,18 @@ __device__ __forceinline__ void deposit_window(int* sJi, const int b[3], const f
     }
 }
 
+// ------------------------------------------------------------ async copies
+
+// 16-byte global -> shared copy that bypasses the registers (completes at
+// cp_async_wait_all of the issuing thread; a block barrier then publishes it).
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 // ------------------------------------------------------------ warp helpers
 
 __device__ __forceinline__ int warp_aggregated_add(int* ctr)
@@ -394,6 +406,31 @@ struct SharedState {
     int ngen[2];             // general-window moves of the chunk
     unsigned bound_bits[2];  // float bits of the chunk's largest |jcoef w D|
 };
+
+// Stored-order passes: start copying the particles of list slots
+// [base, base + cn) into the chunk stage (cell, offsets, momenta, weight;
+// 16-byte pieces of whole frames, which are allocated even past the list's
+// count).  The caller waits with cp_async_wait_all and a block barrier.
+template <class T, int NT>
+__device__ __forceinline__ void stage_chunk_async(const StepDev& d, SharedState<T, NT>& sh, int L, int base,
+                                                  int cn)
+{
+    constexpr int S = T::S;
+    const int* ft = d.ftab + d.foff[L];
+    const int nq = (cn + 3) >> 2;
+    for (int k = threadIdx.x; k < nq; k += NT) {
+        const int slot = base + 4 * k;
+        const int64_t idx = (int64_t)ft[slot >> d.log2S] * S + (slot & (S - 1));
+        cp_async16(sh.st.cell + 4 * k, d.cell + idx);
+        cp_async16(sh.st.o[0] + 4 * k, d.ox + idx);
+        cp_async16(sh.st.o[1] + 4 * k, d.oy + idx);
+        cp_async16(sh.st.o[2] + 4 * k, d.oz + idx);
+        cp_async16(sh.st.u[0] + 4 * k, d.ux + idx);
+        cp_async16(sh.st.u[1] + 4 * k, d.uy + idx);
+        cp_async16(sh.st.u[2] + 4 * k, d.uz + idx);
+        cp_async16(sh.st.w + 4 * k, d.w + idx);
+    }
+}
 
 // ------------------------------------------------------------ deposit of one record
 
@@ -802,14 +839,23 @@ __device__ __forceinline__ void push_list(const StepDev& d, const SpeciesDev& sp
             }
         } else {
             // push in stored order (sorted at the last sort pass, a few
-            // particles displaced since): straight from the pool into
-            // registers and back to the same slot
+            // particles displaced since): from the stage, which an async copy
+            // filled while the previous chunk deposited, and back to the same
+            // slot of the pool
             for (int s0 = 0; s0 < cn; s0 += NT) {
                 const int sidx = s0 + tid;
                 float bnd = 0.0f;
                 if (sidx < cn) {
                     const int64_t idx = gidx(base + sidx);
-                    Part q = load_part(d, idx);
+                    Part q;
+                    q.cell = sh.st.cell[sidx];
+                    q.o[0] = sh.st.o[0][sidx];
+                    q.o[1] = sh.st.o[1][sidx];
+                    q.o[2] = sh.st.o[2][sidx];
+                    q.u[0] = sh.st.u[0][sidx];
+                    q.u[1] = sh.st.u[1][sidx];
+                    q.u[2] = sh.st.u[2][sidx];
+                    q.w = sh.st.w[sidx];
                     bnd = push_one<T, SHAPE, NT>(d, sp, s, bx, scx, scy, scz, sF, sh, q,
                                                  d.pid ? d.pid + idx : nullptr, base + sidx, sidx, cb,
                                                  my_status);
@@ -825,6 +871,8 @@ __device__ __forceinline__ void push_list(const StepDev& d, const SpeciesDev& sp
             sh.ngen[cb ^ 1] = 0;
             sh.bound_bits[cb ^ 1] = 0u;
         }
+        if (!sort_pass && base + C < n)  // the stage is free: the next chunk flies during the deposit
+            stage_chunk_async<T, NT>(d, sh, L, base + C, min(C, n - base - C));
         // deposit: neighbouring lanes take chunk positions kDepStride apart
         // (sorted by node, so one warp's atomics land on different nodes and
         // mostly different banks); then the general-window moves
@@ -847,6 +895,8 @@ __device__ __forceinline__ void push_list(const StepDev& d, const SpeciesDev& sp
         for (int t = ((wid - (nfull >> 5)) % NWARP + NWARP) % NWARP; t < rem; t += NWARP)
             deposit_general_warp<T, SHAPE, C>(sJi, sh.rec, sh.rec.gen[nfull + t], sp.jcoef, scale);
         prev_inv = inv;
+        if (!sort_pass)
+            cp_async_wait_all();
         __syncthreads();
     }
     if (n > 0)
@@ -983,7 +1033,18 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_push_deposit(const StepDev d)
         }
 
 
-        // ---- 1. stage the E/B tile, zero the J tiles
+        // ---- 1. stage the E/B tile, zero the J tiles; on a stored-order pass
+        // the first chunk of the first mobile list is copied meanwhile
+        int pre_s = -1;
+        if (!sort_pass) {
+            for (int s = 0; s < d.nspecies && pre_s < 0; ++s) {
+                const int n = d.count[s * d.nsc + g];
+                if (d.sp[s].mobile && n > 0) {
+                    pre_s = s;
+                    stage_chunk_async<T, NT>(d, sh, s * d.nsc + g, 0, min(SharedState<T, NT>::C, n));
+                }
+            }
+        }
         const int64_t pcell = padded_cells(bx);
         const int64_t start = ((int64_t)(scz * LZ) * bx.py + scy * LY) * bx.px + scx * LX;
         constexpr int ROW4 = TX / 4;
@@ -1018,6 +1079,11 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_push_deposit(const StepDev d)
                 sh.nholes = 0;
                 sh.ngen[0] = 0;
                 sh.bound_bits[0] = 0u;
+            }
+            if (!sort_pass) {
+                if (s != pre_s)
+                    stage_chunk_async<T, NT>(d, sh, L, 0, min(SharedState<T, NT>::C, n));
+                cp_async_wait_all();
             }
             __syncthreads();
             if (sp.shape == 2)
