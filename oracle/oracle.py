@@ -77,7 +77,7 @@ def lib():
             gp = ctypes.POINTER(_Grid)
             L.orc_shape.argtypes = [ctypes.c_int, ctypes.c_double]
             L.orc_shape.restype = ctypes.c_double
-            L.orc_gather.argtypes = [gp, ctypes.c_int, dp, dp, dp, dp, dp]
+            L.orc_gather.argtypes = [gp, ctypes.c_int, dp, dp, dp, dp, dp, ctypes.c_int]
             L.orc_gather.restype = None
             L.orc_boris.argtypes = [ctypes.c_double] * 3 + [dp, dp, dp]
             L.orc_boris.restype = None
@@ -86,7 +86,7 @@ def lib():
             L.orc_deposit_esirkepov.restype = ctypes.c_int
             L.orc_push_deposit.argtypes = [gp, ctypes.c_double, ctypes.c_int, ctypes.c_double,
                                            ctypes.c_double, dp, dp, dp, ctypes.c_int64,
-                                           dp, dp, dp, ctypes.c_int]
+                                           dp, dp, dp, ctypes.c_int, ctypes.c_int]
             L.orc_push_deposit.restype = ctypes.c_int
             L.orc_yee_b.argtypes = [gp, ctypes.c_double, dp, dp]
             L.orc_yee_b.restype = None
@@ -140,12 +140,14 @@ def shape(order: int, d: float) -> float:
     return lib().orc_shape(int(order), float(d))
 
 
-def gather(g: _Grid, order: int, E: np.ndarray, B: np.ndarray, x) -> tuple[np.ndarray, np.ndarray]:
-    """E and B interpolated to one position x (3,) in cell units."""
+def gather(g: _Grid, order: int, E: np.ndarray, B: np.ndarray, x, ec: bool = False) -> tuple[np.ndarray, np.ndarray]:
+    """E and B interpolated to one position x (3,) in cell units; ec: the
+    energy-conserving variant (one order lower along staggered axes)."""
     xp = _f64(x, (3,))
     Ep = np.zeros(3)
     Bp = np.zeros(3)
-    lib().orc_gather(ctypes.byref(g), int(order), _ptr(E), _ptr(B), _ptr(xp), _ptr(Ep), _ptr(Bp))
+    lib().orc_gather(ctypes.byref(g), int(order), _ptr(E), _ptr(B), _ptr(xp), _ptr(Ep), _ptr(Bp),
+                     int(bool(ec)))
     return Ep, Bp
 
 
@@ -232,7 +234,9 @@ def yee_e(g: _Grid, dt: float, E: np.ndarray, B: np.ndarray, J: np.ndarray) -> N
 @dataclass
 class Species:
     """One macro-particle species: charge q, mass m (in e and m_e), shape
-    order (1 = CIC, 2 = TSC), mobile flag, and its particle arrays."""
+    order (1 = CIC, 2 = TSC), mobile flag, its particle arrays, and the
+    gather variant (ec: energy-conserving, one order lower along each
+    staggered axis of a field component)."""
     q: float
     m: float
     order: int
@@ -240,6 +244,7 @@ class Species:
     u: np.ndarray
     w: np.ndarray | None = None
     mobile: bool = True
+    ec: bool = False
 
     def __post_init__(self):
         self.x = _f64(self.x).reshape(-1, 3).copy()
@@ -293,7 +298,7 @@ class State:
                 rc = L.orc_push_deposit(ctypes.byref(self.g), float(self.dt), int(sp.order),
                                         float(sp.q), float(sp.m), _ptr(self.E), _ptr(self.B),
                                         _ptr(self.J), int(sp.x.shape[0]), _ptr(sp.x), _ptr(sp.u),
-                                        _ptr(sp.w), int(bool(self.open_y)))
+                                        _ptr(sp.w), int(bool(self.open_y)), int(bool(sp.ec)))
                 if rc != ORC_OK:
                     raise ValueError(f"oracle push rejected a particle move (code {rc})")
                 if self.open_y:

@@ -70,6 +70,8 @@ static inline int64_t ncells(const orc_grid* g) { return g->nx * g->ny * g->nz; 
 double orc_shape(int order, double d)
 {
     double a = fabs(d);
+    if (order == 0) /* nearest grid point; a point half-way goes to the upper neighbour */
+        return (d >= -0.5 && d < 0.5) ? 1.0 : 0.0;
     if (order == 1)
         return a < 1.0 ? 1.0 - a : 0.0;
     if (order == 2) {
@@ -90,17 +92,22 @@ static const double B_STAGGER[3][3] = {{0.0, 0.5, 0.5}, {0.5, 0.0, 0.5}, {0.5, 0
  * Field gather (Sec. 4, "trilinear interpolation in field gathering", with
  * the TSC shape): F(x_p) = sum over the grid points m of the component of
  * F[m] * S(x_p - m - s) in x, y and z, s being the component's staggering.
- * The window of six points per axis covers the support of both shapes.
+ * The window of six points per axis covers the support of every shape.
+ * ec (energy-conserving variant, beyond the paper): along each axis on which
+ * the component is staggered by half a cell the shape is one order lower
+ * (TSC -> CIC, CIC -> nearest grid point), so that the gather is the
+ * transpose of the Esirkepov current along that axis.
  */
 static double gather_component(const double* F, const orc_grid* g, int order,
-                               const double x[3], const double s[3])
+                               const double x[3], const double s[3], int ec)
 {
     int64_t base[3];
     double wt[3][6];
     for (int d = 0; d < 3; ++d) {
+        int od = (ec && s[d] == 0.5) ? order - 1 : order;
         base[d] = (int64_t)floor(x[d] - s[d]) - 2;
         for (int n = 0; n < 6; ++n)
-            wt[d][n] = orc_shape(order, x[d] - s[d] - (double)(base[d] + n));
+            wt[d][n] = orc_shape(od, x[d] - s[d] - (double)(base[d] + n));
     }
     double sum = 0.0;
     for (int c = 0; c < 6; ++c)
@@ -114,12 +121,12 @@ static double gather_component(const double* F, const orc_grid* g, int order,
 }
 
 void orc_gather(const orc_grid* g, int order, const double* E, const double* B,
-                const double x[3], double Ep[3], double Bp[3])
+                const double x[3], double Ep[3], double Bp[3], int ec)
 {
     int64_t nc = ncells(g);
     for (int c = 0; c < 3; ++c) {
-        Ep[c] = gather_component(E + c * nc, g, order, x, E_STAGGER[c]);
-        Bp[c] = gather_component(B + c * nc, g, order, x, B_STAGGER[c]);
+        Ep[c] = gather_component(E + c * nc, g, order, x, E_STAGGER[c], ec);
+        Bp[c] = gather_component(B + c * nc, g, order, x, B_STAGGER[c], ec);
     }
 }
 
@@ -213,11 +220,12 @@ int orc_deposit_esirkepov(const orc_grid* g, int order, double qw, double dt,
  * (NULL = all weights 1).  J accumulates (the caller zeroes it).  open_y:
  * the y coordinate is not wrapped, so that the caller can remove the
  * particles that left through a y face (they have deposited their current,
- * folded periodically like every other deposit).
+ * folded periodically like every other deposit).  ec: the energy-conserving
+ * gather (see gather_component).
  */
 int orc_push_deposit(const orc_grid* g, double dt, int order, double q, double m,
                      const double* E, const double* B, double* J,
-                     int64_t n, double* x, double* u, const double* w, int open_y)
+                     int64_t n, double* x, double* u, const double* w, int open_y, int ec)
 {
     double h[3] = {g->dx, g->dy, g->dz};
     int64_t N[3] = {g->nx, g->ny, g->nz};
@@ -225,7 +233,7 @@ int orc_push_deposit(const orc_grid* g, double dt, int order, double q, double m
         double* xp = x + 3 * p;
         double* up = u + 3 * p;
         double Ep[3], Bp[3];
-        orc_gather(g, order, E, B, xp, Ep, Bp);
+        orc_gather(g, order, E, B, xp, Ep, Bp, ec);
         orc_boris(q, m, dt, Ep, Bp, up);
         double gam = sqrt(1.0 + up[0] * up[0] + up[1] * up[1] + up[2] * up[2]);
         double x1[3];
