@@ -64,11 +64,21 @@ typedef struct {
 /* One species: charge and mass in units of e and m_e (electron: -1, 1);
  * shape 1 = cloud-in-cell (linear), 2 = triangular-shaped cloud (quadratic
  * spline, the TSC of Sec. 4); mobile = 0 freezes the species (it still
- * counts in the charge density and the diagnostics, and deposits no current). */
+ * counts in the charge density and the diagnostics, and deposits no current).
+ * gather: PIC_GATHER_MOMENTUM (0) interpolates every field component with
+ * the particle's shape on all three axes (the paper's product of 1D
+ * weights); PIC_GATHER_ENERGY (1) uses the shape one order lower along each
+ * axis on which the component is staggered by half a cell (TSC -> CIC,
+ * CIC -> nearest grid point), which makes the gather the transpose of the
+ * Esirkepov current: for motion along one axis the field's work on the
+ * particle equals the current's work on the field.  Not in the paper. */
+enum { PIC_GATHER_MOMENTUM = 0, PIC_GATHER_ENERGY = 1 };
 typedef struct {
     double charge, mass;
     int32_t shape;
     int32_t mobile;
+    int32_t gather;
+    int32_t reserved;
 } pic_species;
 
 /* Precision forms. */

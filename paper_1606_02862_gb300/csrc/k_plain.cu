@@ -29,25 +29,40 @@ __device__ __forceinline__ double S64(int shape, double d)
 }
 
 // Weights of a component sampled at node + s (s = 0 or 1/2) along one axis:
-// first node and NW weights.
+// first node and NW weights.  red: one order lower (the energy-conserving
+// gather along a staggered axis), placed in the same window: CIC inside the
+// TSC window, nearest grid point inside the CIC window.
 template <int SHAPE>
-__device__ __forceinline__ int axis_weights(double x, double s, double* wt)
+__device__ __forceinline__ int axis_weights(double x, double s, double* wt, bool red)
 {
     if (SHAPE == 2) {
         double xs = x - s;
         double n0 = floor(xs + 0.5);
         double dd = xs - n0;
-        double a = 0.5 - dd, c = 0.5 + dd;
-        wt[0] = 0.5 * a * a;
-        wt[1] = 0.75 - dd * dd;
-        wt[2] = 0.5 * c * c;
+        if (red) {  // CIC between floor(xs) and floor(xs) + 1
+            const bool below = dd < 0.0;  // floor(xs) = n0 - 1
+            const double f = below ? dd + 1.0 : dd;
+            wt[0] = below ? 1.0 - f : 0.0;
+            wt[1] = below ? f : 1.0 - f;
+            wt[2] = below ? 0.0 : f;
+        } else {
+            double a = 0.5 - dd, c = 0.5 + dd;
+            wt[0] = 0.5 * a * a;
+            wt[1] = 0.75 - dd * dd;
+            wt[2] = 0.5 * c * c;
+        }
         return (int)n0 - 1;
     } else {
         double xs = x - s;
         double n0 = floor(xs);
         double f = xs - n0;
-        wt[0] = 1.0 - f;
-        wt[1] = f;
+        if (red) {  // nearest of n0, n0 + 1 (a tie goes up)
+            wt[0] = f < 0.5 ? 1.0 : 0.0;
+            wt[1] = f < 0.5 ? 0.0 : 1.0;
+        } else {
+            wt[0] = 1.0 - f;
+            wt[1] = f;
+        }
         return (int)n0;
     }
 }
@@ -55,13 +70,13 @@ __device__ __forceinline__ int axis_weights(double x, double s, double* wt)
 template <int SHAPE>
 __device__ __forceinline__ double gather64(const double* __restrict__ F, int nx, int ny, int nz,
                                            double x, double y, double z, double sx, double sy,
-                                           double sz)
+                                           double sz, bool ec)
 {
     constexpr int NW = SHAPE == 2 ? 3 : 2;
     double wx[NW], wy[NW], wz[NW];
-    int bx = axis_weights<SHAPE>(x, sx, wx);
-    int by = axis_weights<SHAPE>(y, sy, wy);
-    int bz = axis_weights<SHAPE>(z, sz, wz);
+    int bx = axis_weights<SHAPE>(x, sx, wx, ec && sx != 0.0);
+    int by = axis_weights<SHAPE>(y, sy, wy, ec && sy != 0.0);
+    int bz = axis_weights<SHAPE>(z, sz, wz, ec && sz != 0.0);
     double acc = 0.0;
 #pragma unroll
     for (int c = 0; c < NW; ++c) {
@@ -89,12 +104,13 @@ __global__ void __launch_bounds__(256) k_plain_push(const PlainPushArgs a)
     const int nx = a.nx, ny = a.ny, nz = a.nz;
     const int64_t nc = (int64_t)nx * ny * nz;
     const double x0 = a.x[i], y0 = a.y[i], z0 = a.z[i];
-    const double Ex = gather64<SHAPE>(a.E, nx, ny, nz, x0, y0, z0, 0.5, 0.0, 0.0);
-    const double Ey = gather64<SHAPE>(a.E + nc, nx, ny, nz, x0, y0, z0, 0.0, 0.5, 0.0);
-    const double Ez = gather64<SHAPE>(a.E + 2 * nc, nx, ny, nz, x0, y0, z0, 0.0, 0.0, 0.5);
-    const double Bx = gather64<SHAPE>(a.B, nx, ny, nz, x0, y0, z0, 0.0, 0.5, 0.5);
-    const double By = gather64<SHAPE>(a.B + nc, nx, ny, nz, x0, y0, z0, 0.5, 0.0, 0.5);
-    const double Bz = gather64<SHAPE>(a.B + 2 * nc, nx, ny, nz, x0, y0, z0, 0.5, 0.5, 0.0);
+    const bool ec = a.ec != 0;
+    const double Ex = gather64<SHAPE>(a.E, nx, ny, nz, x0, y0, z0, 0.5, 0.0, 0.0, ec);
+    const double Ey = gather64<SHAPE>(a.E + nc, nx, ny, nz, x0, y0, z0, 0.0, 0.5, 0.0, ec);
+    const double Ez = gather64<SHAPE>(a.E + 2 * nc, nx, ny, nz, x0, y0, z0, 0.0, 0.0, 0.5, ec);
+    const double Bx = gather64<SHAPE>(a.B, nx, ny, nz, x0, y0, z0, 0.0, 0.5, 0.5, ec);
+    const double By = gather64<SHAPE>(a.B + nc, nx, ny, nz, x0, y0, z0, 0.5, 0.0, 0.5, ec);
+    const double Bz = gather64<SHAPE>(a.B + 2 * nc, nx, ny, nz, x0, y0, z0, 0.5, 0.5, 0.0, ec);
 
     // relativistic Boris push
     const double eps = a.eps;

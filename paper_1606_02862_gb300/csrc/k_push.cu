@@ -145,13 +145,15 @@ __host__ __device__ __forceinline__ float cic_dS(float d0, float D)
 // sampled at integer nodes along this axis, "h" = at half nodes.  For the
 // integer nodes the weights are also the particle's shape S0 at the nodes
 // a-1, a, a+1 (TSC, a = round(o)) or 0, 1 (CIC): the deposit reuses them.
+// red: the energy-conserving variant, one order lower at the half nodes
+// (CIC inside the TSC window, nearest node inside the CIC window).
 template <int SHAPE>
 struct AxisW {
     static constexpr int NW = SHAPE == 2 ? 3 : 2;
     int bi, bh;  // tile index of the first node
     float wi[NW], wh[NW];
     float di;    // TSC: o - a
-    __device__ __forceinline__ AxisW(int l, float o)
+    __device__ __forceinline__ AxisW(int l, float o, bool red)
     {
         if (SHAPE == 2) {
             bool up = o >= 0.5f;
@@ -162,11 +164,17 @@ struct AxisW {
             wi[1] = 0.75f - di * di;
             wi[2] = 0.5f * c * c;
             float dh = o - 0.5f;
-            bh = l;
-            float ah = 0.5f - dh, ch = 0.5f + dh;
-            wh[0] = 0.5f * ah * ah;
-            wh[1] = 0.75f - dh * dh;
-            wh[2] = 0.5f * ch * ch;
+            bh = l;  // half nodes l - 1/2, l + 1/2, l + 3/2
+            if (red) {
+                wh[0] = up ? 0.0f : 0.5f - o;
+                wh[1] = up ? 1.5f - o : 0.5f + o;
+                wh[2] = up ? o - 0.5f : 0.0f;
+            } else {
+                float ah = 0.5f - dh, ch = 0.5f + dh;
+                wh[0] = 0.5f * ah * ah;
+                wh[1] = 0.75f - dh * dh;
+                wh[2] = 0.5f * ch * ch;
+            }
         } else {
             di = o;
             bi = l + 1;
@@ -174,9 +182,9 @@ struct AxisW {
             wi[1] = o;
             bool up = o >= 0.5f;
             float dh = up ? o - 0.5f : o + 0.5f;
-            bh = l + (up ? 1 : 0);
-            wh[0] = 1.0f - dh;
-            wh[1] = dh;
+            bh = l + (up ? 1 : 0);  // half nodes bh - 1/2 .. : the cell's own is l + 1/2
+            wh[0] = red ? (up ? 1.0f : 0.0f) : 1.0f - dh;
+            wh[1] = red ? (up ? 0.0f : 1.0f) : dh;
         }
     }
 };
@@ -620,7 +628,8 @@ __device__ __forceinline__ float push_one(const StepDev& d, const SpeciesDev& sp
     const int lz = cell / (LX * LY);
 
     // gather (Sec. 4: product of 1D weights at each Yee position)
-    AxisW<SHAPE> ax(lx, ox), ay(ly, oy), az(lz, oz);
+    const bool ec = sp.ec != 0;
+    AxisW<SHAPE> ax(lx, ox, ec), ay(ly, oy, ec), az(lz, oz, ec);
     const float Ex = gather_comp<NW, PX, TY>(sF + 0 * N, ax.bh, ay.bi, az.bi, ax.wh, ay.wi, az.wi);
     const float Ey = gather_comp<NW, PX, TY>(sF + 1 * N, ax.bi, ay.bh, az.bi, ax.wi, ay.wh, az.wi);
     const float Ez = gather_comp<NW, PX, TY>(sF + 2 * N, ax.bi, ay.bi, az.bh, ax.wi, ay.wi, az.wh);

@@ -306,6 +306,7 @@ StepDev make_step(const pic_ctx* c, int parity)
         q.m = (float)p.mass;
         q.shape = p.shape;
         q.mobile = p.mobile;
+        q.ec = p.gather == PIC_GATHER_ENERGY;
         float jmax = std::max({std::fabs(q.jcoef[0]), std::fabs(q.jcoef[1]), std::fabs(q.jcoef[2])});
         q.cbound = jmax * c->wmax[s] * 1.0001f;  // headroom for FP32 rounding
     }
@@ -645,6 +646,7 @@ PlainPushArgs plain_args(const pic_ctx* c, int box, int species)
     a.w = s.w;
     const double V = c->h[0] * c->h[1] * c->h[2];
     a.eps = p.charge * c->dt / (2.0 * p.mass);
+    a.ec = p.gather == PIC_GATHER_ENERGY;
     for (int d = 0; d < 3; ++d) {
         a.jcoef[d] = -p.charge * c->h[d] / (V * c->dt);
         a.move[d] = c->dt / c->h[d];
@@ -755,7 +757,8 @@ pic_status pic_create(const pic_grid* grids, int32_t nboxes, const double dx[3],
         if (grids[b].nx < 4 || grids[b].ny < 4 || grids[b].nz < 4)
             return PIC_ERR_ARG;
     for (int s = 0; s < nspecies; ++s)
-        if (!(sp[s].mass > 0.0) || !std::isfinite(sp[s].charge) || (sp[s].shape != 1 && sp[s].shape != 2))
+        if (!(sp[s].mass > 0.0) || !std::isfinite(sp[s].charge) || (sp[s].shape != 1 && sp[s].shape != 2) ||
+            (sp[s].gather != PIC_GATHER_MOMENTUM && sp[s].gather != PIC_GATHER_ENERGY))
             return PIC_ERR_ARG;
     // no particle may cross half a cell per step (|v| < c), and the Yee
     // scheme must be stable

@@ -50,7 +50,7 @@ struct SpeciesDev {
     int shape;        // 1 CIC, 2 TSC
     int mobile;
     float cbound;     // max over d of |jcoef[d]| * max weight: bounds |q w P T| / (V dt) terms
-    int pad;
+    int ec;           // energy-conserving gather (one order lower along staggered axes)
 };
 
 // Open-y options of a box (pic_set_boundary, pic_set_antenna).

@@ -17,6 +17,7 @@ struct PlainPushArgs {
     double jcoef[3];  // -q h_d / (V dt)
     double move[3];   // dt / h_d
     unsigned* status;
+    int ec;           // energy-conserving gather
 };
 
 struct PlainYeeArgs {

@@ -48,9 +48,13 @@ class Grid(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32)]
 
 
+GATHER_MOMENTUM, GATHER_ENERGY = 0, 1
+
+
 class SpeciesC(ctypes.Structure):
     _fields_ = [("charge", ctypes.c_double), ("mass", ctypes.c_double),
-                ("shape", ctypes.c_int32), ("mobile", ctypes.c_int32)]
+                ("shape", ctypes.c_int32), ("mobile", ctypes.c_int32),
+                ("gather", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class Boundary(ctypes.Structure):
@@ -142,6 +146,7 @@ class Species:
     mass: float
     shape: int = 2
     mobile: bool = True
+    gather: int = GATHER_MOMENTUM
 
 
 class _TorchMemory:
@@ -183,7 +188,8 @@ class Context:
         self.precision = precision
         garr = (Grid * len(grids))(*[Grid(*g) for g in grids])
         sarr = (SpeciesC * len(self.species))(*[SpeciesC(float(s.charge), float(s.mass), int(s.shape),
-                                                         int(bool(s.mobile))) for s in self.species])
+                                                         int(bool(s.mobile)), int(s.gather), 0)
+                                                for s in self.species])
         dxa = (ctypes.c_double * 3)(*self.dx)
         o = Options()
         o.precision = int(precision)
@@ -364,7 +370,8 @@ def from_workload(wl, precision=PRECISION_MIXED, sc=(4, 4, 4), threads_per_sc=0,
                   use_graph=True, **kw) -> Context:
     """Create a context for a workloads.Workload and load its initial state."""
     ctx = Context([(b.nx, b.ny, b.nz) for b in wl.boxes], wl.dx, wl.dt,
-                  [Species(s.q, s.m, s.shape, s.mobile) for s in wl.species], precision=precision,
+                  [Species(s.q, s.m, s.shape, s.mobile, GATHER_ENERGY if getattr(s, "ec", False)
+                           else GATHER_MOMENTUM) for s in wl.species], precision=precision,
                   sc=sc, threads_per_sc=threads_per_sc, track_ids=track_ids, use_graph=use_graph,
                   **kw)
     extra = getattr(wl, "extra", None) or {}

@@ -46,6 +46,7 @@ class SpeciesDef:
     m: float
     shape: int  # 1 = CIC, 2 = TSC
     mobile: bool = True
+    ec: bool = False  # energy-conserving gather
 
 
 @dataclass

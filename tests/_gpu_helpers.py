@@ -37,7 +37,7 @@ def oracle_state_from_gpu(orc, ctx, wl, box, **state_kw):
         order = np.argsort(p["id"])
         ids.append(p["id"][order])
         osp = orc.Species(q=sd.q, m=sd.m, order=sd.shape, x=p["x"][order], u=p["u"][order],
-                          w=p["w"][order], mobile=sd.mobile)
+                          w=p["w"][order], mobile=sd.mobile, ec=getattr(sd, "ec", False))
         osp.ids = p["id"][order]
         species.append(osp)
     st = orc.State(b.nx, b.ny, b.nz, wl.dt, dx=wl.dx, E=E, B=B, species=species, rho_bg=b.rho_bg,

@@ -66,4 +66,6 @@ def test_create_rejects_bad_arguments_without_touching_the_device(libpath):
     assert L.pic_create(g, 1, dx, 0.2, bad, 1, None, ctypes.byref(ctx)) == 1
     bad = (pic.SpeciesC * 1)(pic.SpeciesC(-1.0, 0.0, 2, 1))
     assert L.pic_create(g, 1, dx, 0.2, bad, 1, None, ctypes.byref(ctx)) == 1
+    bad = (pic.SpeciesC * 1)(pic.SpeciesC(-1.0, 1.0, 2, 1, 2, 0))  # no gather mode 2
+    assert L.pic_create(g, 1, dx, 0.2, bad, 1, None, ctypes.byref(ctx)) == 1
     assert not ctx.value

@@ -207,3 +207,26 @@ def test_diagnostics_match_oracle(orc):
     rho_scale = np.max(np.abs(st.rho()))
     assert abs(got[3] - want[3]) < 1e-5 * rho_scale
     ctx.close()
+
+
+@pytest.mark.parametrize("pre", [0, 2], ids=["sort_pass", "stored_order"])
+@pytest.mark.parametrize("shape", [1, 2])
+def test_mixed_energy_conserving_gather(orc, shape, pre):
+    """The energy-conserving gather variant (one order lower along each
+    staggered axis) against the oracle's, two species with the variant on
+    one of them."""
+    from paper_1606_02862_gb300 import workloads as W
+
+    wl = _thermal(n=(16, 16, 16), shape=shape, u_th=0.1, species="ions", fields=0.05)
+    wl.species[0] = W.SpeciesDef("e", -1.0, 1.0, shape, True, True)
+    _one_step_parity(orc, wl, MIXED_TOL, pre_steps=pre, sc=(8, 4, 4), threads_per_sc=256)
+
+
+@pytest.mark.parametrize("shape", [1, 2])
+def test_plain_energy_conserving_gather(orc, shape):
+    from paper_1606_02862_gb300 import pic
+    from paper_1606_02862_gb300 import workloads as W
+
+    wl = _thermal(shape=shape, u_th=0.1, fields=0.05)
+    wl.species[0] = W.SpeciesDef("e", -1.0, 1.0, shape, True, True)
+    _one_step_parity(orc, wl, PLAIN_TOL, precision=pic.PRECISION_FP64_PLAIN)
