@@ -168,11 +168,14 @@ def make_state(torch, n, ppc, u_th, pinned=True):
 SHAPE = {"tsc": 2, "cic": 1}
 
 
-def new_ctx(pic, n, precision, sc, threads, shape=2):
+GATHER = {"momentum": 0, "energy": 1}
+
+
+def new_ctx(pic, n, precision, sc, threads, shape=2, gather=0):
     from paper_1606_02862_gb300 import workloads as W
 
     ctx = pic.Context([(n, n, n)], (1.0, 1.0, 1.0), W.DT_HALF_COURANT,
-                      [pic.Species(-1.0, 1.0, shape, True)], precision=precision, sc=sc,
+                      [pic.Species(-1.0, 1.0, shape, True, gather)], precision=precision, sc=sc,
                       threads_per_sc=threads, use_graph=True)
     ctx.set_background(0, 0.01)
     return ctx
@@ -319,7 +322,7 @@ def run_ours(args, rank, world, dist):
     result = {}
 
     # ---------------- mixed form, device-resident inputs, graph replay
-    ctx = new_ctx(pic, n, pic.PRECISION_MIXED, sc, args.threads, SHAPE[args.shape])
+    ctx = new_ctx(pic, n, pic.PRECISION_MIXED, sc, args.threads, SHAPE[args.shape], GATHER[args.gather])
     t0 = time.perf_counter()
     load(ctx, X, U, Wt)
     log(f"[rank {rank}] loaded in {time.perf_counter() - t0:.1f} s")
@@ -368,7 +371,7 @@ def run_ours(args, rank, world, dist):
         Eo = np.empty((3, n, n, n))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        ctx = new_ctx(pic, n, pic.PRECISION_MIXED, sc, args.threads, SHAPE[args.shape])
+        ctx = new_ctx(pic, n, pic.PRECISION_MIXED, sc, args.threads, SHAPE[args.shape], GATHER[args.gather])
         load(ctx, X, U, Wt)
         ctx.step(args.steps)
         nout = ctx.read_particles_ptr(0, 0, npart, Xo.data_ptr(), Uo.data_ptr(), Wo.data_ptr())
@@ -387,7 +390,7 @@ def run_ours(args, rank, world, dist):
 
     # ---------------- plain FP64 GPU form, same workload
     if not args.no_plain:
-        ctx = new_ctx(pic, n, pic.PRECISION_FP64_PLAIN, sc, 0, SHAPE[args.shape])
+        ctx = new_ctx(pic, n, pic.PRECISION_FP64_PLAIN, sc, 0, SHAPE[args.shape], GATHER[args.gather])
         load(ctx, X, U, Wt)
         ctx.step(1)
         ctx.stage_timing(True)
@@ -419,7 +422,8 @@ def run_ours(args, rank, world, dist):
         "data": "synthetic",
         "config": {"workload": f"thermal_{args.shape}_{n}: {n}^3 periodic cells, electrons {ppc} ppc "
                                f"({npart} particles/GPU), u_th 0.05c, {args.shape.upper()}, "
-                               "dt = 0.5 Courant, neutralising background",
+                               "dt = 0.5 Courant, neutralising background"
+                               + (", energy-conserving gather" if args.gather == "energy" else ""),
                    "form": f"mixed: int32 cell + FP32 offsets, supercell frames {args.sc}, "
                            f"{args.threads or 'default'} threads/supercell",
                    "graph": result["graph"],
@@ -640,6 +644,8 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--shape", default="tsc", choices=["tsc", "cic"],
                     help="particle shape of the headline thermal workload")
+    ap.add_argument("--gather", default="momentum", choices=["momentum", "energy"],
+                    help="gather variant of the headline thermal workload")
     ap.add_argument("--workload", default="thermal_tsc_256",
                     choices=["thermal_tsc_256", "small_cic_32", "laser_ramp", "foil_overdense",
                              "khi_128", "laser_window"])
