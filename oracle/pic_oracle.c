@@ -64,8 +64,11 @@ static inline int64_t ncells(const orc_grid* g) { return g->nx * g->ny * g->nz; 
 /*
  * 1D assignment functions of Hockney & Eastwood, which Sec. 4 names for the
  * particle shape: order 1 = cloud-in-cell (linear), order 2 = triangular-
- * shaped cloud (quadratic spline).  d is the distance from the particle to a
- * grid point, in cells.
+ * shaped cloud (quadratic spline); beyond the paper, order 3 = piecewise
+ * cubic spline (PCS) and order 0 = nearest grid point (used only by the
+ * energy-conserving gather).  d is the distance from the particle to a grid
+ * point, in cells.  The six-point windows of the gather and the deposit
+ * below cover the support of every order up to 3 for moves below one cell.
  */
 double orc_shape(int order, double d)
 {
@@ -79,6 +82,13 @@ double orc_shape(int order, double d)
             return 0.75 - a * a;
         if (a < 1.5)
             return 0.5 * (1.5 - a) * (1.5 - a);
+        return 0.0;
+    }
+    if (order == 3) { /* piecewise cubic spline (PCS, the cubic B-spline) */
+        if (a < 1.0)
+            return (4.0 - 6.0 * a * a + 3.0 * a * a * a) / 6.0;
+        if (a < 2.0)
+            return (2.0 - a) * (2.0 - a) * (2.0 - a) / 6.0;
         return 0.0;
     }
     return 0.0;

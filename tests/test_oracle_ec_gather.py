@@ -91,7 +91,7 @@ def _line_integral(orc, g, order, E, B, x0, axis, D, ec):
     """int_0^1 E_axis(x0 + s D e_axis) D ds, split where the gathered
     component is not smooth (integer and half-integer positions along the
     axis) and integrated by 4-point Gauss-Legendre on each piece (exact for
-    the piecewise polynomials of degree <= 7 that a gather of order <= 2 gives)."""
+    the piecewise polynomials of degree <= 7 that a gather of order <= 3 gives)."""
     a, b = x0[axis], x0[axis] + D
     lo, hi = min(a, b), max(a, b)
     cuts = [lo] + [k / 2.0 for k in range(int(np.floor(lo * 2)) + 1, int(np.ceil(hi * 2)))] + [hi]
@@ -106,7 +106,7 @@ def _line_integral(orc, g, order, E, B, x0, axis, D, ec):
     return tot if D > 0 else -tot
 
 
-@pytest.mark.parametrize("order", [1, 2])
+@pytest.mark.parametrize("order", [1, 2, 3])
 @pytest.mark.parametrize("axis", [0, 1, 2])
 def test_energy_identity_for_motion_along_one_axis(orc, order, axis):
     """sum J.E over the cells (Esirkepov, q w = 1, dt = V = 1) equals the line

@@ -44,7 +44,7 @@ def _moves(rng, n, count, maxd):
     return x0, d
 
 
-@pytest.mark.parametrize("order", [1, 2])
+@pytest.mark.parametrize("order", [1, 2, 3])
 @pytest.mark.parametrize("h", [(1.0, 1.0, 1.0), (0.7, 1.3, 1.0)])
 def test_continuity_random_moves(orc, order, h):
     n = 8
@@ -62,7 +62,7 @@ def test_continuity_random_moves(orc, order, h):
         assert np.max(np.abs(res)) < 1e-13 * scale
 
 
-@pytest.mark.parametrize("order", [1, 2])
+@pytest.mark.parametrize("order", [1, 2, 3])
 def test_total_current_is_particle_current(orc, order):
     n = 8
     h = (1.0, 0.9, 1.2)
@@ -77,7 +77,7 @@ def test_total_current_is_particle_current(orc, order):
             assert abs(J[c].sum() * V - qw * dd[c] * h[c] / DT) < 1e-13
 
 
-@pytest.mark.parametrize("order", [1, 2])
+@pytest.mark.parametrize("order", [1, 2, 3])
 def test_time_reversal(orc, order):
     n = 8
     g = orc.grid(n, n, n)
@@ -94,7 +94,7 @@ def test_every_face_edge_and_corner_crossing(orc):
     not at all): continuity and total current for both shapes."""
     n = 6
     g = orc.grid(n, n, n)
-    for order in (1, 2):
+    for order in (1, 2, 3):
         for start in ([2.95, 3.02, 2.97], [3.5, 3.5, 3.5], [2.51, 2.49, 3.0]):
             for dirn in itertools.product((-1, 0, 1), repeat=3):
                 a = np.array(start)
@@ -140,7 +140,7 @@ def test_cic_within_cell_equals_charge_flux(orc):
         assert np.max(np.abs(J[0] - want[0])) < 1e-13
 
 
-@pytest.mark.parametrize("order", [1, 2])
+@pytest.mark.parametrize("order", [1, 2, 3])
 def test_equals_average_over_axis_orderings(orc, order):
     """Build J from 1D continuity alone: move one axis at a time; a move along
     d carries J_d(m_d + 1/2) = -(dx_d/dt) q w / V * prefix sum over m' <= m_d

@@ -4,7 +4,8 @@ and a product-of-1D-weights gather; CIC is the linear shape).
 What fixes the values independently of the oracle's code:
   * B-spline identities: every shape sums to one over the integer grid points
     and reproduces the first moment (sum of n S(x - n) is x), for any x;
-  * the support widths (2 points for CIC, 3 for TSC) and the textbook values
+  * the support widths (2 points for CIC, 3 for TSC, 4 for PCS), the second
+    moment of the B-spline of order n, (n + 1) / 12, and the textbook values
     at the centre and at the half-cell points;
   * a gather of a uniform field returns the field; a gather of a field that
     is linear in space, sampled at each component's staggered Yee position,
@@ -15,7 +16,7 @@ import numpy as np
 import pytest
 
 
-@pytest.mark.parametrize("order", [1, 2])
+@pytest.mark.parametrize("order", [1, 2, 3])
 def test_partition_of_unity_and_first_moment(orc, order):
     rng = np.random.default_rng(1)
     for x in np.concatenate([rng.uniform(-5, 5, 200), [0.0, 0.5, -0.5, 1.0, 2.5]]):
@@ -25,6 +26,9 @@ def test_partition_of_unity_and_first_moment(orc, order):
         assert abs(s.sum() - 1.0) < 1e-15
         assert abs((nodes * s).sum() - x) < 1e-13
         assert np.count_nonzero(s) <= order + 1
+        # second moment of the B-spline of order n: variance (n + 1) / 12
+        if order > 1:
+            assert abs((((x - nodes) ** 2) * s).sum() - (order + 1) / 12.0) < 1e-13
 
 
 def test_textbook_values():
@@ -37,6 +41,12 @@ def test_textbook_values():
     assert orc.shape(2, 0.5) == 0.5 and orc.shape(2, -0.5) == 0.5
     assert orc.shape(2, 1.0) == 0.125 and orc.shape(2, -1.0) == 0.125
     assert orc.shape(2, 1.5) == 0.0 and orc.shape(2, 2.0) == 0.0
+    # PCS (the cubic B-spline): 2/3 at the centre, 1/6 at one cell, 1/48 at 3/2, 0 at 2
+    assert orc.shape(3, 0.0) == pytest.approx(2.0 / 3.0, abs=1e-16)
+    assert orc.shape(3, 1.0) == pytest.approx(1.0 / 6.0, abs=1e-16)
+    assert orc.shape(3, -1.5) == pytest.approx(1.0 / 48.0, abs=1e-16)
+    assert orc.shape(3, 0.5) == pytest.approx(23.0 / 48.0, abs=1e-16)
+    assert orc.shape(3, 2.0) == 0.0 and orc.shape(3, -2.5) == 0.0
     # continuity of the spline and of its slope at |d| = 1/2
     eps = 1e-7
     assert abs(orc.shape(2, 0.5 - eps) - 0.5) < 1.01 * eps
@@ -60,7 +70,7 @@ def _field_from(fn, n, stagger):
     return out
 
 
-@pytest.mark.parametrize("order", [1, 2])
+@pytest.mark.parametrize("order", [1, 2, 3])
 def test_gather_uniform_field(orc, order):
     n = 8
     g = orc.grid(n, n, n)
@@ -76,7 +86,7 @@ def test_gather_uniform_field(orc, order):
         assert np.allclose(Bp, [2.4, -1.6, -0.5], rtol=0, atol=1e-14)
 
 
-@pytest.mark.parametrize("order", [1, 2])
+@pytest.mark.parametrize("order", [1, 2, 3])
 def test_gather_linear_field_at_staggered_positions(orc, order):
     """A wrong staggering offset (1/2 cell) or a swapped axis moves the result
     by slope/2 or by (slope_a - slope_b) * coordinate and fails here."""
