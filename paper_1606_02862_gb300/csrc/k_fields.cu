@@ -66,27 +66,39 @@ __device__ __forceinline__ CellAt yee_cell(const YeeArgs& a, const BoxDev*& bp)
     return c;
 }
 
-// Periodic images of an interior coordinate inside the padded range
-// (x: -1 .. n+2, y and z: -1 .. n+1).  Returns the count (1..2), [0] = itself.
-__device__ __forceinline__ int images(int v, int n, int hi_guard, int* out)
+// Periodic images of an interior coordinate v in [0, n) inside the padded
+// range [-lo, n + hi): v itself, v + n when v < hi, v - n when v >= n - lo
+// (boxes are at least as large as the guards, so no second wrap).  Returns
+// the count (1..3), [0] = v.
+__device__ __forceinline__ int images(int v, int n, int lo, int hi, int* out)
 {
     out[0] = v;
-    if (v < hi_guard) {
-        out[1] = v + n;
-        return 2;
-    }
-    if (v == n - 1) {
-        out[1] = -1;
-        return 2;
-    }
-    return 1;
+    int k = 1;
+    if (v < hi)
+        out[k++] = v + n;
+    if (v >= n - lo)
+        out[k++] = v - n;
+    return k;
+}
+
+__device__ __forceinline__ int images_x(const BoxDev& b, int v, int* out)
+{
+    return images(v, b.nx, b.gx, b.px - b.nx - b.gx, out);
+}
+__device__ __forceinline__ int images_y(const BoxDev& b, int v, int* out)
+{
+    return images(v, b.ny, b.gy, b.py - b.ny - b.gy, out);
+}
+__device__ __forceinline__ int images_z(const BoxDev& b, int v, int* out)
+{
+    return images(v, b.nz, b.gz, b.pz - b.nz - b.gz, out);
 }
 
 __device__ __forceinline__ void store_with_images(const BoxDev& b, float* F, const CellAt& c,
                                                   float v)
 {
-    int ix[2], iy[2], iz[2];
-    int nx = images(c.x, b.nx, 3, ix), ny = images(c.y, b.ny, 2, iy), nz = images(c.z, b.nz, 2, iz);
+    int ix[3], iy[3], iz[3];
+    int nx = images_x(b, c.x, ix), ny = images_y(b, c.y, iy), nz = images_z(b, c.z, iz);
     for (int k = 0; k < nz; ++k)
         for (int j = 0; j < ny; ++j)
             for (int i = 0; i < nx; ++i)
@@ -161,8 +173,8 @@ __global__ void __launch_bounds__(256) k_yee_e(const YeeArgs a)
     const int64_t sx = 1, sy = b.px, sz = (int64_t)b.px * b.py;
     const int64_t i = padded_index(b, c.x, c.y, c.z);
     // fold the J guard images into the interior
-    int ix[2], iy[2], iz[2];
-    int nx = images(c.x, b.nx, 3, ix), ny = images(c.y, b.ny, 2, iy), nz = images(c.z, b.nz, 2, iz);
+    int ix[3], iy[3], iz[3];
+    int nx = images_x(b, c.x, ix), ny = images_y(b, c.y, iy), nz = images_z(b, c.z, iz);
     float jx = 0.f, jy = 0.f, jz = 0.f;
     for (int k = 0; k < nz; ++k)
         for (int j = 0; j < ny; ++j)
@@ -377,6 +389,11 @@ __device__ __forceinline__ double shape64(int shape, double d)
     double a = fabs(d);
     if (shape == 1)
         return a < 1.0 ? 1.0 - a : 0.0;
+    if (shape == 3) {  // PCS
+        if (a < 1.0)
+            return (4.0 - 6.0 * a * a + 3.0 * a * a * a) / 6.0;
+        return a < 2.0 ? (2.0 - a) * (2.0 - a) * (2.0 - a) / 6.0 : 0.0;
+    }
     if (a <= 0.5)
         return 0.75 - a * a;
     return a < 1.5 ? 0.5 * (1.5 - a) * (1.5 - a) : 0.0;

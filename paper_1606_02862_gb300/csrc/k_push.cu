@@ -56,12 +56,17 @@ constexpr int kHoleCap = 256;
 // share a node) or C / 32 (random over the tile).
 constexpr int kDepStride = 4;
 
-template <int LX_, int LY_, int LZ_>
+// G = guard cells below the supercell (the fields' global guards match):
+// 1 for CIC/TSC, 2 when a PCS species is present (its support reaches two
+// nodes below the cell and, for a move across a cell face, three above).
+template <int LX_, int LY_, int LZ_, int G_ = 1>
 struct Tile {
-    static constexpr int LX = LX_, LY = LY_, LZ = LZ_;
-    static constexpr int TX = LX + 4;  // x: one guard below, three above (16-byte rows)
-    static constexpr int TY = LY + 3;  // y, z: one guard below, two above
-    static constexpr int TZ = LZ + 3;
+    static constexpr int LX = LX_, LY = LY_, LZ = LZ_, G = G_;
+    static constexpr int GO = G - 1;  // tile index of node l - 1 is l + GO
+    // x: G below, 3 (CIC/TSC) / 6 (PCS) above, 16-byte rows; y, z: G below, 2 / 3 above
+    static constexpr int TX = G == 1 ? LX + 4 : LX + 8;
+    static constexpr int TY = G == 1 ? LY + 3 : LY + 5;
+    static constexpr int TZ = G == 1 ? LZ + 3 : LZ + 5;
     static constexpr int PX = TX + 1;  // odd shared-memory row pitch
     static constexpr int N = PX * TY * TZ;  // shared floats per component
     static constexpr int S = LX * LY * LZ;
@@ -140,6 +145,51 @@ __host__ __device__ __forceinline__ float cic_dS(float d0, float D)
     return 0.0f;
 }
 
+// PCS (cubic B-spline) at distance d.
+__host__ __device__ __forceinline__ float pcs_S(float d)
+{
+    const float a = fabsf(d);
+    if (a < 1.0f)
+        return (4.0f - 6.0f * a * a + 3.0f * a * a * a) * (1.0f / 6.0f);
+    const float t = fmaxf(2.0f - a, 0.0f);
+    return t * t * t * (1.0f / 6.0f);
+}
+
+// S(d0 + D) - S(d0) on one spline piece (the piece of the segment's midpoint),
+// factored through D: central piece (|d| < 1, sign s fixed)
+//   D [-(d0 + d1) + s (d0^2 + d0 d1 + d1^2) / 2],
+// outer piece (1 <= |d| < 2, a = 2 - s d)   -s D (a0^2 + a0 a1 + a1^2) / 6.
+__host__ __device__ __forceinline__ float pcs_seg(float d0, float D)
+{
+    const float d1 = d0 + D;
+    const float m = d0 + 0.5f * D;
+    const float s = m >= 0.0f ? 1.0f : -1.0f;
+    const float am = fabsf(m);
+    if (am < 1.0f)
+        return D * (-(d0 + d1) + 0.5f * s * (d0 * d0 + d0 * d1 + d1 * d1));
+    if (am < 2.0f) {
+        const float a0 = 2.0f - s * d0, a1 = 2.0f - s * d1;
+        return -s * D * (a0 * a0 + a0 * a1 + a1 * a1) * (1.0f / 6.0f);
+    }
+    return 0.0f;
+}
+
+// S(d0 + D) - S(d0) for PCS without forming the difference of two values:
+// the pieces join at the integers (the spline is C2 there), and a move of
+// less than half a cell crosses at most one join p, where the difference is
+// split at p with the exact distance p - d0.
+__host__ __device__ __forceinline__ float pcs_dS(float d0, float D)
+{
+    const float d1 = d0 + D;  // classification only
+    const float lo = fminf(d0, d1), hi = fmaxf(d0, d1);
+    const float p = floorf(hi);
+    if (p > lo && fabsf(p) <= 2.0f) {
+        const float u = p - d0;
+        return pcs_seg(d0, u) + pcs_seg(p, D - u);
+    }
+    return pcs_seg(d0, D);
+}
+
 // Gather weights along one axis for a particle at offset o in [0,1) of its
 // cell; the tile coordinate of the particle's cell is l + 1.  "i" = field
 // sampled at integer nodes along this axis, "h" = at half nodes.  For the
@@ -147,15 +197,39 @@ __host__ __device__ __forceinline__ float cic_dS(float d0, float D)
 // a-1, a, a+1 (TSC, a = round(o)) or 0, 1 (CIC): the deposit reuses them.
 // red: the energy-conserving variant, one order lower at the half nodes
 // (CIC inside the TSC window, nearest node inside the CIC window).
+// l is the tile index of node (cell - 1): cell + GO.
 template <int SHAPE>
 struct AxisW {
-    static constexpr int NW = SHAPE == 2 ? 3 : 2;
+    static constexpr int NW = SHAPE == 2 ? 3 : (SHAPE == 3 ? 4 : 2);
     int bi, bh;  // tile index of the first node
     float wi[NW], wh[NW];
     float di;    // TSC: o - a
     __device__ __forceinline__ AxisW(int l, float o, bool red)
     {
-        if (SHAPE == 2) {
+        if (SHAPE == 3) {
+            // integer nodes cell-1 .. cell+2; half nodes m0 .. m0+3 with
+            // m0 = cell - 2 + up (the half node m + 1/2 is stored at index m)
+            di = o;
+            bi = l;
+            wi[0] = pcs_S(o + 1.0f);
+            wi[1] = pcs_S(o);
+            wi[2] = pcs_S(o - 1.0f);
+            wi[3] = pcs_S(o - 2.0f);
+            const bool up = o >= 0.5f;
+            bh = l - 1 + (up ? 1 : 0);
+            if (red) {  // TSC at the half nodes cell-1, cell, cell+1
+                const float a = 1.0f - o, c = o, m = 0.75f - (o - 0.5f) * (o - 0.5f);
+                wh[0] = up ? 0.5f * a * a : 0.0f;
+                wh[1] = up ? m : 0.5f * a * a;
+                wh[2] = up ? 0.5f * c * c : m;
+                wh[3] = up ? 0.0f : 0.5f * c * c;
+            } else {
+                const float h = o + (up ? 0.5f : 1.5f);  // distance to half node m0
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    wh[k] = pcs_S(h - (float)k);
+            }
+        } else if (SHAPE == 2) {
             bool up = o >= 0.5f;
             di = up ? o - 1.0f : o;
             bi = l + (up ? 1 : 0);
@@ -442,14 +516,15 @@ __device__ __forceinline__ void stage_chunk_async(const StepDev& d, SharedState<
 
 // ------------------------------------------------------------ deposit of one record
 
-// Common window: nodes a-1, a, a+1 (TSC, a = round(o)) or 0, 1 (CIC) on every
-// axis; S0 is the particle's shape there and DS has closed forms in D.
+// Common window: nodes a-1, a, a+1 (TSC, a = round(o)), 0, 1 (CIC) or -1 .. 2
+// (PCS) relative to the cell on every axis; S0 is the particle's shape there
+// and DS has closed forms in D.  The record's l holds cell + GO per axis.
 template <class T, int SHAPE, int C>
 __device__ __forceinline__ void deposit_common(int* sJi, const Records<C>& r, int s, const float jc[3],
                                                float scale)
 {
     const int e = rslot(s);
-    constexpr int NW = SHAPE == 2 ? 3 : 2;
+    constexpr int NW = SHAPE == 2 ? 3 : (SHAPE == 3 ? 4 : 2);
     const int l = r.l[e];
     const int lc[3] = {l & 0xff, (l >> 8) & 0xff, (l >> 16) & 0xff};
     float S0[3][NW], DS[3][NW];
@@ -470,6 +545,21 @@ __device__ __forceinline__ void deposit_common(int* sJi, const Records<C>& r, in
             DS[a][0] = -0.5f * D * (1.0f - sum);
             DS[a][1] = -D * sum;
             DS[a][2] = 0.5f * D * (1.0f + sum);
+        } else if (SHAPE == 3) {
+            // nodes cell-1 .. cell+2, each on one spline piece for the whole move:
+            // outer (a = 1 - o), centre (d = o), centre (d = o - 1), outer (a = o)
+            b[a] = lc[a];
+            const float o1 = o + D;
+            const float a0 = 1.0f - o, a1 = a0 - D;
+            const float d0 = o - 1.0f, d1 = o1 - 1.0f;
+            S0[a][0] = a0 * a0 * a0 * (1.0f / 6.0f);
+            S0[a][1] = (4.0f - 6.0f * o * o + 3.0f * o * o * o) * (1.0f / 6.0f);
+            S0[a][2] = (4.0f - 6.0f * d0 * d0 - 3.0f * d0 * d0 * d0) * (1.0f / 6.0f);
+            S0[a][3] = o * o * o * (1.0f / 6.0f);
+            DS[a][0] = -D * (a0 * a0 + a0 * a1 + a1 * a1) * (1.0f / 6.0f);
+            DS[a][1] = D * (-(o + o1) + 0.5f * (o * o + o * o1 + o1 * o1));
+            DS[a][2] = D * (-(d0 + d1) - 0.5f * (d0 * d0 + d0 * d1 + d1 * d1));
+            DS[a][3] = D * (o * o + o * o1 + o1 * o1) * (1.0f / 6.0f);
         } else {
             b[a] = lc[a] + 1;
             S0[a][0] = 1.0f - o;
@@ -483,84 +573,115 @@ __device__ __forceinline__ void deposit_common(int* sJi, const Records<C>& r, in
                                            jc[1] * ws, jc[2] * ws);
 }
 
-// General window: nodes l-1 .. l+2 on every axis.
+// Window of the general deposit: M nodes per axis; on axis a its first node
+// sits at tile index lc + first_off(o, D) and node k of the window is at
+// distance d0 = o - node_off(o, D, k) from the particle.
+template <int SHAPE>
+struct GenWin {
+    static constexpr int M = SHAPE == 3 ? 5 : 4;
+    // PCS: nodes cell-2+up .. cell+2+up, up = the move ends in the next cell;
+    // CIC / TSC: nodes cell-1 .. cell+2
+    __device__ __forceinline__ static int first(float o, float D) { return SHAPE == 3 ? (o + D >= 1.0f) - 1 : 0; }
+    __device__ __forceinline__ static float d0(float o, int first, int k) { return o - (float)(k - 1 + first); }
+    __device__ __forceinline__ static float S(float d) { return SHAPE == 3 ? pcs_S(d) : (SHAPE == 2 ? tsc_S(d) : cic_S(d)); }
+    __device__ __forceinline__ static float dS(float d, float D)
+    {
+        return SHAPE == 3 ? pcs_dS(d, D) : (SHAPE == 2 ? tsc_dS(d, D) : cic_dS(d, D));
+    }
+};
+
+// General window (GenWin) on every axis.
 template <class T, int SHAPE, int C>
 __device__ __forceinline__ void deposit_general(int* sJi, const Records<C>& r, int s, const float jc[3],
                                                 float scale)
 {
+    using W = GenWin<SHAPE>;
+    constexpr int M = W::M;
     const int e = rslot(s);
     const int l = r.l[e];
-    float S0[3][4], DS[3][4];
+    const int lc[3] = {l & 0xff, (l >> 8) & 0xff, (l >> 16) & 0xff};  // node cell-1 sits at tile index lc
+    float S0[3][M], DS[3][M];
+    int b[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         const float o = r.o[a][e], D = r.D[a][e];
+        const int f = W::first(o, D);
+        b[a] = lc[a] + f;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const float d0 = o - (float)(k - 1);
-            S0[a][k] = SHAPE == 2 ? tsc_S(d0) : cic_S(d0);
-            DS[a][k] = SHAPE == 2 ? tsc_dS(d0, D) : cic_dS(d0, D);
+        for (int k = 0; k < M; ++k) {
+            const float d0 = W::d0(o, f, k);
+            S0[a][k] = W::S(d0);
+            DS[a][k] = W::dS(d0, D);
         }
     }
-    const int b[3] = {l & 0xff, (l >> 8) & 0xff, (l >> 16) & 0xff};  // node l-1 sits at tile index l
     const float ws = r.w[e] * scale;
-    deposit_window<4, T::PX, T::TY, T::N>(sJi, b, S0[0], S0[1], S0[2], DS[0], DS[1], DS[2], jc[0] * ws,
+    deposit_window<M, T::PX, T::TY, T::N>(sJi, b, S0[0], S0[1], S0[2], DS[0], DS[1], DS[2], jc[0] * ws,
                                           jc[1] * ws, jc[2] * ws);
 }
 
 // General window of one move, deposited by a whole warp (all 32 lanes
-// converged): lane 4a + k evaluates S0 and DS at node l - 1 + k of axis a and
-// the prefix P of DS along that axis; then each lane adds one or two of the
-// window's 48 lines (a component c and its transverse nodes p, q: three half
-// nodes along c), taking the factors it needs from the other lanes.
+// converged): lane 8a + k (k < M) evaluates S0 and DS at node k of axis a's
+// window and the prefix P of DS along that axis; then the lanes take the
+// window's 3 M^2 lines (a component c and its transverse nodes p, q: M - 1
+// half nodes along c) in turns, reading the factors they need from the
+// lanes that hold them.
 template <class T, int SHAPE, int C>
 __device__ __forceinline__ void deposit_general_warp(int* sJi, const Records<C>& r, int s,
                                                      const float jc[3], float scale)
 {
+    using W = GenWin<SHAPE>;
+    constexpr int M = W::M;
     constexpr unsigned FULL = 0xffffffffu;
     constexpr int PX = T::PX, PY = T::PX * T::TY, NJ = T::N;
     const int lane = threadIdx.x & 31;
     const int e = rslot(s);
     const int l = r.l[e];
-    float s0v = 0.0f, dsv = 0.0f;
-    if (lane < 12) {
-        const int a = lane >> 2, k = lane & 3;
-        const float d0 = r.o[a][e] - (float)(k - 1);
-        const float D = r.D[a][e];
-        s0v = SHAPE == 2 ? tsc_S(d0) : cic_S(d0);
-        dsv = SHAPE == 2 ? tsc_dS(d0, D) : cic_dS(d0, D);
-    }
-    float pv = dsv;  // inclusive prefix over k within each group of 4 lanes
-    float t = __shfl_up_sync(FULL, pv, 1, 4);
-    if ((lane & 3) >= 1)
-        pv += t;
-    t = __shfl_up_sync(FULL, pv, 2, 4);
-    if ((lane & 3) >= 2)
-        pv += t;
-    const float ws = r.w[e] * scale;
-    const int b0 = l & 0xff, b1 = (l >> 8) & 0xff, b2 = (l >> 16) & 0xff;
-    const int base = b2 * PY + b1 * PX + b0;
+    int f[3];
 #pragma unroll
-    for (int round = 0; round < 2; ++round) {
-        const int L = lane + 32 * round;  // line: c = L / 16, p = L % 4, q = (L / 4) % 4
-        const int c = L >> 4;
+    for (int a = 0; a < 3; ++a)
+        f[a] = W::first(r.o[a][e], r.D[a][e]);  // same address in every lane: broadcasts
+    float s0v = 0.0f, dsv = 0.0f;
+    if ((lane & 7) < M && lane < 24) {
+        const int a = lane >> 3, k = lane & 7;
+        const float o = r.o[a][e], D = r.D[a][e];
+        const float d0 = W::d0(o, a == 0 ? f[0] : (a == 1 ? f[1] : f[2]), k);
+        s0v = W::S(d0);
+        dsv = W::dS(d0, D);
+    }
+    float pv = dsv;  // inclusive prefix over k within each group of 8 lanes
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) {
+        const float t = __shfl_up_sync(FULL, pv, o, 8);
+        if ((lane & 7) >= o)
+            pv += t;
+    }
+    const float ws = r.w[e] * scale;
+    const int b0 = (l & 0xff) + f[0], b1 = ((l >> 8) & 0xff) + f[1], b2 = ((l >> 16) & 0xff) + f[2];
+    const int base = b2 * PY + b1 * PX + b0;
+    constexpr int LINES = 3 * M * M;
+#pragma unroll
+    for (int round = 0; round < (LINES + 31) / 32; ++round) {
+        const int L = lane + 32 * round;  // c = L / M^2, p = L % M, q = (L / M) % M
+        const int c = L / (M * M);
         const int ea = c == 2 ? 0 : c + 1, fa = c == 0 ? 2 : c - 1;  // transverse axes
-        const int p = L & 3, q = (L >> 2) & 3;
-        const int srcE = 4 * ea + p, srcF = 4 * fa + q;
-        const float s0e = __shfl_sync(FULL, s0v, srcE), dse = __shfl_sync(FULL, dsv, srcE);
-        const float s0f = __shfl_sync(FULL, s0v, srcF), dsf = __shfl_sync(FULL, dsv, srcF);
-        const float P0 = __shfl_sync(FULL, pv, 4 * (c & 3));
-        const float P1 = __shfl_sync(FULL, pv, 4 * (c & 3) + 1);
-        const float P2 = __shfl_sync(FULL, pv, 4 * (c & 3) + 2);
-        if (L < 48) {
+        const int p = L % M, q = (L / M) % M;
+        const int srcE = 8 * ea + p, srcF = 8 * fa + q;
+        const float s0e = __shfl_sync(FULL, s0v, srcE & 31), dse = __shfl_sync(FULL, dsv, srcE & 31);
+        const float s0f = __shfl_sync(FULL, s0v, srcF & 31), dsf = __shfl_sync(FULL, dsv, srcF & 31);
+        float P[M - 1];
+#pragma unroll
+        for (int i = 0; i < M - 1; ++i)
+            P[i] = __shfl_sync(FULL, pv, (8 * c + i) & 31);
+        if (L < LINES) {
             const float cf = (c == 0 ? jc[0] : (c == 1 ? jc[1] : jc[2])) * ws;
             const float Tv = cf * esk_T(s0e, dse, s0f, dsf);
             const int st_c = c == 0 ? 1 : (c == 1 ? PX : PY);
             const int st_e = ea == 0 ? 1 : (ea == 1 ? PX : PY);
             const int st_f = fa == 0 ? 1 : (fa == 1 ? PX : PY);
             int* at = sJi + c * NJ + base + p * st_e + q * st_f;
-            atomicAdd(at, magic_int(P0 * Tv));
-            atomicAdd(at + st_c, magic_int(P1 * Tv));
-            atomicAdd(at + 2 * st_c, magic_int(P2 * Tv));
+#pragma unroll
+            for (int i = 0; i < M - 1; ++i)
+                atomicAdd(at + i * st_c, magic_int(P[i] * Tv));
         }
     }
 }
@@ -617,7 +738,8 @@ __device__ __forceinline__ float push_one(const StepDev& d, const SpeciesDev& sp
                                          int sidx, int cb, unsigned& my_status)
 {
     constexpr int LX = T::LX, LY = T::LY, LZ = T::LZ, N = T::N, PX = T::PX, TY = T::TY;
-    constexpr int NW = SHAPE == 2 ? 3 : 2;
+    constexpr int NW = SHAPE == 2 ? 3 : (SHAPE == 3 ? 4 : 2);
+    constexpr int GO = T::GO;
     auto& rec = sh.rec;
     const int cell = q.cell;
     const float ox = q.o[0], oy = q.o[1], oz = q.o[2];
@@ -629,7 +751,7 @@ __device__ __forceinline__ float push_one(const StepDev& d, const SpeciesDev& sp
 
     // gather (Sec. 4: product of 1D weights at each Yee position)
     const bool ec = sp.ec != 0;
-    AxisW<SHAPE> ax(lx, ox, ec), ay(ly, oy, ec), az(lz, oz, ec);
+    AxisW<SHAPE> ax(lx + GO, ox, ec), ay(ly + GO, oy, ec), az(lz + GO, oz, ec);
     const float Ex = gather_comp<NW, PX, TY>(sF + 0 * N, ax.bh, ay.bi, az.bi, ax.wh, ay.wi, az.wi);
     const float Ey = gather_comp<NW, PX, TY>(sF + 1 * N, ax.bi, ay.bh, az.bi, ax.wi, ay.wh, az.wi);
     const float Ez = gather_comp<NW, PX, TY>(sF + 2 * N, ax.bi, ay.bi, az.bh, ax.wi, ay.wi, az.wh);
@@ -667,7 +789,7 @@ __device__ __forceinline__ float push_one(const StepDev& d, const SpeciesDev& sp
     else
         common = x1 >= 0.0f && x1 < 1.0f && y1 >= 0.0f && y1 < 1.0f && z1 >= 0.0f && z1 < 1.0f;
     const int rs = rslot(sidx);
-    rec.l[rs] = lx | (ly << 8) | (lz << 16) | (common ? 0 : (1 << 24));
+    rec.l[rs] = (lx + GO) | ((ly + GO) << 8) | ((lz + GO) << 16) | (common ? 0 : (1 << 24));
     rec.o[0][rs] = ox;
     rec.o[1][rs] = oy;
     rec.o[2][rs] = oz;
@@ -679,8 +801,8 @@ __device__ __forceinline__ float push_one(const StepDev& d, const SpeciesDev& sp
         rec.gen[atomicAdd(&sh.ngen[cb], 1)] = sidx;
     // bound on every current term of this particle: |jcoef_d w P| with |P| <= |D_d|
     // (P is a difference of cumulative shape sums, whose slope is at most 1),
-    // times |T| <= (max S)^2: 9/16 for TSC (S <= 3/4), 1 for CIC
-    const float tmax = SHAPE == 2 ? 0.5625f * 1.001f : 1.0f;
+    // times |T| <= (max S)^2: 9/16 for TSC (S <= 3/4), 4/9 for PCS (S <= 2/3), 1 for CIC
+    const float tmax = SHAPE == 2 ? 0.5625f * 1.001f : (SHAPE == 3 ? (4.0f / 9.0f) * 1.001f : 1.0f);
     const float bnd = tmax * fabsf(w) * fmaxf(fmaxf(fabsf(sp.jcoef[0] * Dx), fabsf(sp.jcoef[1] * Dy)),
                                               fabsf(sp.jcoef[2] * Dz));
 
@@ -995,7 +1117,7 @@ __device__ __forceinline__ void compact_list(const StepDev& d, int L, int n, int
 // ------------------------------------------------------------ the kernel
 
 template <class T, int NT>
-__global__ void __launch_bounds__(NT, 1024 / NT) k_push_deposit(const StepDev d)
+__global__ void __launch_bounds__(NT, (T::G == 1 ? 1024 : 512) / NT) k_push_deposit(const StepDev d)
 {
     constexpr int TX = T::TX, TY = T::TY, TZ = T::TZ, PX = T::PX, N = T::N;
     constexpr int LX = T::LX, LY = T::LY, LZ = T::LZ;
@@ -1097,6 +1219,9 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_push_deposit(const StepDev d)
             __syncthreads();
             if (sp.shape == 2)
                 push_list<T, 2, NT>(d, sp, s, g, bx, scx, scy, scz, sF, sJi, sJf, sh, sort_pass, my_status);
+            else if (T::G == 2 && sp.shape == 3)
+                push_list<T, T::G == 2 ? 3 : 1, NT>(d, sp, s, g, bx, scx, scy, scz, sF, sJi, sJf, sh, sort_pass,
+                                                    my_status);
             else
                 push_list<T, 1, NT>(d, sp, s, g, bx, scx, scy, scz, sF, sJi, sJf, sh, sort_pass, my_status);
             const int nh = sh.nholes;
@@ -1160,39 +1285,43 @@ static cudaError_t launch_one(const StepDev& d, int grid, cudaStream_t st)
     return cudaGetLastError();
 }
 
+// (supercell edges, threads, guard): guard 1 for CIC/TSC contexts, 2 for
+// contexts with a PCS species
 #define PIC_PUSH_CASES(X)  \
-    X(4, 4, 4, 64)         \
-    X(4, 4, 4, 128)        \
-    X(4, 4, 4, 256)        \
-    X(8, 4, 4, 128)        \
-    X(8, 4, 4, 256)        \
-    X(8, 8, 4, 128)        \
-    X(8, 8, 4, 256)        \
-    X(8, 8, 8, 256)
+    X(4, 4, 4, 64, 1)      \
+    X(4, 4, 4, 128, 1)     \
+    X(4, 4, 4, 256, 1)     \
+    X(8, 4, 4, 128, 1)     \
+    X(8, 4, 4, 256, 1)     \
+    X(8, 8, 4, 128, 1)     \
+    X(8, 8, 4, 256, 1)     \
+    X(8, 8, 8, 256, 1)     \
+    X(4, 4, 4, 128, 2)     \
+    X(8, 4, 4, 256, 2)
 
-size_t push_smem_bytes(int LX, int LY, int LZ, int threads)
+size_t push_smem_bytes(int LX, int LY, int LZ, int threads, int guard)
 {
-#define X(a, b, c, t)                                          \
-    if (LX == a && LY == b && LZ == c && threads == t)         \
-        return dyn_smem<Tile<a, b, c>, t>();
+#define X(a, b, c, t, g)                                                   \
+    if (LX == a && LY == b && LZ == c && threads == t && guard == g)       \
+        return dyn_smem<Tile<a, b, c, g>, t>();
     PIC_PUSH_CASES(X)
 #undef X
     return 0;
 }
 
-int push_supported(int LX, int LY, int LZ, int threads)
+int push_supported(int LX, int LY, int LZ, int threads, int guard)
 {
-#define X(a, b, c, t) if (LX == a && LY == b && LZ == c && threads == t) return 1;
+#define X(a, b, c, t, g) if (LX == a && LY == b && LZ == c && threads == t && guard == g) return 1;
     PIC_PUSH_CASES(X)
 #undef X
     return 0;
 }
 
-cudaError_t configure_push(int LX, int LY, int LZ, int threads, int* per_sm)
+cudaError_t configure_push(int LX, int LY, int LZ, int threads, int guard, int* per_sm)
 {
-#define X(a, b, c, t)                                          \
-    if (LX == a && LY == b && LZ == c && threads == t)         \
-        return configure_one<Tile<a, b, c>, t>(per_sm);
+#define X(a, b, c, t, g)                                                   \
+    if (LX == a && LY == b && LZ == c && threads == t && guard == g)       \
+        return configure_one<Tile<a, b, c, g>, t>(per_sm);
     PIC_PUSH_CASES(X)
 #undef X
     return cudaErrorInvalidValue;
@@ -1200,9 +1329,9 @@ cudaError_t configure_push(int LX, int LY, int LZ, int threads, int* per_sm)
 
 cudaError_t launch_push_deposit(const StepDev& d, int threads, int grid, cudaStream_t st)
 {
-#define X(a, b, c, t)                                          \
-    if (d.LX == a && d.LY == b && d.LZ == c && threads == t)   \
-        return launch_one<Tile<a, b, c>, t>(d, grid, st);
+#define X(a, b, c, t, g)                                                   \
+    if (d.LX == a && d.LY == b && d.LZ == c && threads == t && d.guard == g) \
+        return launch_one<Tile<a, b, c, g>, t>(d, grid, st);
     PIC_PUSH_CASES(X)
 #undef X
     return cudaErrorInvalidValue;

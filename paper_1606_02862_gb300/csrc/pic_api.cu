@@ -66,6 +66,7 @@ struct pic_ctx {
     size_t stage_bytes = 0;
     // mixed form
     int LX = 4, LY = 4, LZ = 4, S = 64, log2S = 6, threads = 64;
+    int guard = 1;  // field guard cells below the interior: 2 when a species has the PCS shape
     int push_grid = 0;
     std::vector<BoxDev> boxes_h;
     BoxDev* boxes_d = nullptr;
@@ -285,6 +286,7 @@ StepDev make_step(const pic_ctx* c, int parity)
     d.LZ = c->LZ;
     d.S = c->S;
     d.log2S = c->log2S;
+    d.guard = c->guard;
     d.nboxes = c->nboxes;
     d.nsc = c->nsc;
     d.nspecies = (int)c->sp.size();
@@ -495,7 +497,7 @@ pic_status prepare_mixed(pic_ctx* c)
                                           : std::max<int64_t>(1 << 20, c->total_particles / 6);
     CKS(ensure_mv(c, mv));
     int per_sm = 0;
-    CK(configure_push(c->LX, c->LY, c->LZ, c->threads, &per_sm));
+    CK(configure_push(c->LX, c->LY, c->LZ, c->threads, c->guard, &per_sm));
     c->push_grid = std::max(1, per_sm) * c->nsm;
     c->prepared = true;
     return PIC_OK;
@@ -757,7 +759,7 @@ pic_status pic_create(const pic_grid* grids, int32_t nboxes, const double dx[3],
         if (grids[b].nx < 4 || grids[b].ny < 4 || grids[b].nz < 4)
             return PIC_ERR_ARG;
     for (int s = 0; s < nspecies; ++s)
-        if (!(sp[s].mass > 0.0) || !std::isfinite(sp[s].charge) || (sp[s].shape != 1 && sp[s].shape != 2) ||
+        if (!(sp[s].mass > 0.0) || !std::isfinite(sp[s].charge) || sp[s].shape < 1 || sp[s].shape > 3 ||
             (sp[s].gather != PIC_GATHER_MOMENTUM && sp[s].gather != PIC_GATHER_ENERGY))
             return PIC_ERR_ARG;
     // no particle may cross half a cell per step (|v| < c), and the Yee
@@ -819,6 +821,9 @@ pic_status pic_create(const pic_grid* grids, int32_t nboxes, const double dx[3],
         return bail(PIC_ERR_OOM);
 
     if (c->precision == PIC_PRECISION_FP64_PLAIN) {
+        for (int s = 0; s < nspecies; ++s)
+            if (sp[s].shape == 3)
+                return bail(PIC_ERR_ARG);  // the plain form has CIC and TSC only
         c->pboxes.resize(nboxes);
         for (int b = 0; b < nboxes; ++b) {
             int64_t nc = (int64_t)grids[b].nx * grids[b].ny * grids[b].nz;
@@ -839,9 +844,12 @@ pic_status pic_create(const pic_grid* grids, int32_t nboxes, const double dx[3],
         c->log2S = ilog2(c->S);
         c->threads = o.threads_per_sc > 0 ? o.threads_per_sc : (c->S >= 256 ? 256 : 128);
         c->sort_every = o.sort_every > 0 ? o.sort_every : kDefaultSortEvery;
-        if ((1 << c->log2S) != c->S || !push_supported(c->LX, c->LY, c->LZ, c->threads))
+        for (int s = 0; s < nspecies; ++s)
+            if (sp[s].shape == 3)
+                c->guard = 2;
+        if ((1 << c->log2S) != c->S || !push_supported(c->LX, c->LY, c->LZ, c->threads, c->guard))
             return bail(PIC_ERR_ARG);
-        if (push_smem_bytes(c->LX, c->LY, c->LZ, c->threads) > c->smem_optin)
+        if (push_smem_bytes(c->LX, c->LY, c->LZ, c->threads, c->guard) > c->smem_optin)
             return bail(PIC_ERR_ARG);
         // boxes
         c->boxes_h.resize(nboxes);
@@ -852,13 +860,19 @@ pic_status pic_create(const pic_grid* grids, int32_t nboxes, const double dx[3],
             const pic_grid& g = grids[b];
             if (g.nx % c->LX || g.ny % c->LY || g.nz % c->LZ)
                 return bail(PIC_ERR_ARG);
+            if (c->guard == 2 && g.nx < 8)  // one periodic image per guard cell
+                return bail(PIC_ERR_ARG);
             BoxDev& bd = c->boxes_h[b];
             bd.nx = g.nx;
             bd.ny = g.ny;
             bd.nz = g.nz;
-            bd.px = g.nx + 4;
-            bd.py = g.ny + 3;
-            bd.pz = g.nz + 3;
+            // guards: TSC/CIC tiles reach 1 cell below and 3 (x, 16-byte rows) /
+            // 2 (y, z) above; PCS tiles 2 below and 6 (x) / 3 (y, z) above
+            const int G = c->guard;
+            bd.gx = bd.gy = bd.gz = G;
+            bd.px = g.nx + (G == 1 ? 4 : 8);
+            bd.py = g.ny + (G == 1 ? 3 : 5);
+            bd.pz = g.nz + (G == 1 ? 3 : 5);
             bd.nscx = g.nx / c->LX;
             bd.nscy = g.ny / c->LY;
             bd.nscz = g.nz / c->LZ;

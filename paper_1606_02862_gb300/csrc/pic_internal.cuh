@@ -3,9 +3,11 @@
 // Mixed form (int32 cell + FP32 offset particles, FP32 fields):
 //
 //   Fields of a box live in guard-padded arrays, one array per component,
-//   x fastest: padded index = ((z+1)*py + (y+1))*px + (x+1) for the real cell
-//   (x, y, z), with px = nx + 4 (guards: 1 below, 3 above), py = ny + 3,
-//   pz = nz + 3 (1 below, 2 above).  E and B guards hold periodic copies of
+//   x fastest: padded index = ((z+gz)*py + (y+gy))*px + (x+gx) for the real
+//   cell (x, y, z).  CIC/TSC contexts: g = 1, px = nx + 4 (guards: 1 below, 3
+//   above), py = ny + 3, pz = nz + 3 (1 below, 2 above).  Contexts with a PCS
+//   species: g = 2, px = nx + 8 (2 below, 6 above), py = ny + 5, pz = nz + 5
+//   (2 below, 3 above).  E and B guards hold periodic copies of
 //   the interior (rewritten by every Yee half update); J guards collect
 //   deposits that the Yee E update folds back into the periodic images.  The
 //   padding lets every supercell read its E/B tile and write its J tile as one
@@ -65,6 +67,7 @@ struct OpenYDev {
 struct BoxDev {
     int nx, ny, nz;
     int px, py, pz;           // padded extents
+    int gx, gy, gz;           // guard cells below the interior (above: p - n - g)
     int nscx, nscy, nscz;     // supercells per axis
     int sc_base;              // first global supercell id of the box
     float* E;                 // 3 * px*py*pz, component-major
@@ -77,6 +80,7 @@ struct BoxDev {
 struct StepDev {
     // geometry
     int LX, LY, LZ, S, log2S;  // supercell edges, frame size
+    int guard;                 // field guard cells below the interior (1, or 2 with PCS)
     int nboxes, nsc, nspecies, nlists;
     float dt;
     float move[3];            // dt / h_d
@@ -138,7 +142,7 @@ struct StepDev {
 
 __host__ __device__ inline int64_t padded_index(const BoxDev& b, int x, int y, int z)
 {
-    return ((int64_t)(z + 1) * b.py + (y + 1)) * b.px + (x + 1);
+    return ((int64_t)(z + b.gz) * b.py + (y + b.gy)) * b.px + (x + b.gx);
 }
 
 __host__ __device__ inline int64_t padded_cells(const BoxDev& b)
@@ -164,10 +168,10 @@ struct YeePlan {
     int abs_nblocks;
     int antenna;               // nonzero: some box has an antenna (launch k_antenna)
 };
-cudaError_t configure_push(int LX, int LY, int LZ, int threads, int* per_sm);
+cudaError_t configure_push(int LX, int LY, int LZ, int threads, int guard, int* per_sm);
 cudaError_t launch_push_deposit(const StepDev& d, int threads, int grid, cudaStream_t st);
-int push_supported(int LX, int LY, int LZ, int threads);
-size_t push_smem_bytes(int LX, int LY, int LZ, int threads);
+int push_supported(int LX, int LY, int LZ, int threads, int guard);
+size_t push_smem_bytes(int LX, int LY, int LZ, int threads, int guard);
 int frame_scan_blocks(int nlists);
 cudaError_t launch_frame_plan(const StepDev& d, cudaStream_t st);
 cudaError_t launch_frame_apply(const StepDev& d, int place_blocks, cudaStream_t st);

@@ -62,8 +62,9 @@ def test_create_rejects_bad_arguments_without_touching_the_device(libpath):
     assert L.pic_create(g, 1, dx, 0.6, sp, 1, None, ctypes.byref(ctx)) == 2
     # zero boxes, bad shape, nonpositive mass
     assert L.pic_create(g, 0, dx, 0.2, sp, 1, None, ctypes.byref(ctx)) == 1
-    bad = (pic.SpeciesC * 1)(pic.SpeciesC(-1.0, 1.0, 3, 1))
-    assert L.pic_create(g, 1, dx, 0.2, bad, 1, None, ctypes.byref(ctx)) == 1
+    for shape in (0, 4):  # 1 CIC, 2 TSC, 3 PCS
+        bad = (pic.SpeciesC * 1)(pic.SpeciesC(-1.0, 1.0, shape, 1))
+        assert L.pic_create(g, 1, dx, 0.2, bad, 1, None, ctypes.byref(ctx)) == 1
     bad = (pic.SpeciesC * 1)(pic.SpeciesC(-1.0, 0.0, 2, 1))
     assert L.pic_create(g, 1, dx, 0.2, bad, 1, None, ctypes.byref(ctx)) == 1
     bad = (pic.SpeciesC * 1)(pic.SpeciesC(-1.0, 1.0, 2, 1, 2, 0))  # no gather mode 2

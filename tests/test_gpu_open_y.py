@@ -13,7 +13,7 @@ pytestmark = pytest.mark.gpu
 TOL = dict(tol_field=1e-5, tol_x=1e-5, tol_u=1e-5)
 
 
-def _plasma(nx=16, ny=32, nz=16, ppc=4, u_th=0.1, fields=1e-2, seed=0, y_range=None):
+def _plasma(nx=16, ny=32, nz=16, ppc=4, u_th=0.1, fields=1e-2, seed=0, y_range=None, shape=2):
     from paper_1606_02862_gb300 import workloads as W
 
     rng = np.random.default_rng(4000 + seed)
@@ -25,7 +25,7 @@ def _plasma(nx=16, ny=32, nz=16, ppc=4, u_th=0.1, fields=1e-2, seed=0, y_range=N
     E = rng.normal(0, fields, (3, nz, ny, nx))
     B = rng.normal(0, fields, (3, nz, ny, nx))
     box = W.BoxInit(nx, ny, nz, particles=[(x, u, w)], E=E, B=B, rho_bg=0.01)
-    return W.Workload("open_y_test", W.DT_HALF_COURANT, [W.SpeciesDef("e", -1.0, 1.0, 2)], [box])
+    return W.Workload("open_y_test", W.DT_HALF_COURANT, [W.SpeciesDef("e", -1.0, 1.0, shape)], [box])
 
 
 def _step_and_compare(orc, ctx, wl, state_kw, tol=TOL):
@@ -38,10 +38,10 @@ def _step_and_compare(orc, ctx, wl, state_kw, tol=TOL):
     return st
 
 
-@pytest.mark.parametrize("pre", [0, 2])
-def test_absorber_one_step(orc, pre):
+@pytest.mark.parametrize("pre,shape", [(0, 2), (2, 2), (1, 3)])
+def test_absorber_one_step(orc, pre, shape):
     require_gpu()
-    wl = _plasma()
+    wl = _plasma(shape=shape)
     ctx = ctx_from(wl, sc=(8, 4, 4), threads_per_sc=256)
     try:
         ctx.set_boundary(0, absorber_cells=8, absorber_sigma=0.5)
@@ -127,12 +127,13 @@ def test_antenna_vacuum_run_matches_oracle(orc):
         ctx.close()
 
 
-def test_window_shift_then_step(orc):
+@pytest.mark.parametrize("shape", [2, 3])
+def test_window_shift_then_step(orc, shape):
     from paper_1606_02862_gb300 import pic
     from paper_1606_02862_gb300 import workloads as W
 
     require_gpu()
-    wl = _plasma(ny=32)
+    wl = _plasma(ny=32, shape=shape)
     ctx = ctx_from(wl, sc=(8, 4, 4), threads_per_sc=256)
     try:
         ctx.set_boundary(0, open_y=True, absorber_cells=4, absorber_sigma=0.2)

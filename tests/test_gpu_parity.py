@@ -230,3 +230,77 @@ def test_plain_energy_conserving_gather(orc, shape):
     wl = _thermal(shape=shape, u_th=0.1, fields=0.05)
     wl.species[0] = W.SpeciesDef("e", -1.0, 1.0, shape, True, True)
     _one_step_parity(orc, wl, PLAIN_TOL, precision=pic.PRECISION_FP64_PLAIN)
+
+
+# ---------------------------------------------------------------- PCS shape
+
+PCS_CONFIGS = [((4, 4, 4), 128), ((8, 4, 4), 256)]
+
+
+@pytest.mark.parametrize("pre", [0, 2], ids=["sort_pass", "stored_order"])
+@pytest.mark.parametrize("sc,threads", PCS_CONFIGS)
+def test_mixed_pcs_one_step(orc, sc, threads, pre):
+    """The PCS (cubic spline) shape: 4-node gather, 4-node common and 5-node
+    general Esirkepov windows, 2-cell field guards."""
+    wl = _thermal(n=(16, 24, 16), shape=3, u_th=0.1)
+    _one_step_parity(orc, wl, MIXED_TOL, pre_steps=pre, sc=sc, threads_per_sc=threads)
+
+
+@pytest.mark.parametrize("other", [1, 2])
+def test_mixed_pcs_with_cic_or_tsc_species(orc, other):
+    """A CIC or TSC species in a context whose tiles carry the PCS guards
+    (every tile index shifted by one), next to a PCS species."""
+    from paper_1606_02862_gb300 import workloads as W
+
+    wl = _thermal(n=(16, 16, 16), shape=other, u_th=0.3, species="ions", fields=0.05)
+    wl.species[1] = W.SpeciesDef("p", 1.0, W.PROTON_MASS, 3)
+    _one_step_parity(orc, wl, MIXED_TOL, sc=(8, 4, 4), threads_per_sc=256)
+    _one_step_parity(orc, wl, MIXED_TOL, pre_steps=2, sc=(8, 4, 4), threads_per_sc=256)
+
+
+def test_mixed_pcs_energy_conserving_gather(orc):
+    from paper_1606_02862_gb300 import workloads as W
+
+    wl = _thermal(n=(16, 16, 16), shape=3, u_th=0.1, fields=0.05)
+    wl.species[0] = W.SpeciesDef("e", -1.0, 1.0, 3, True, True)
+    _one_step_parity(orc, wl, MIXED_TOL, pre_steps=1, sc=(4, 4, 4), threads_per_sc=128)
+
+
+def test_mixed_pcs_edge_positions(orc):
+    """Particles on and next to cell faces, supercell and box seams, moving
+    across them: the 5-node general window."""
+    from paper_1606_02862_gb300 import workloads as W
+
+    n = 8
+    pts, us = [], []
+    for base in ([0.0, 0.0, 0.0], [3.999999, 4.0, 7.9999995], [7.5, 3.5, 0.5], [4.0, 4.0, 4.0],
+                 [0.02, 7.97, 3.01]):
+        for dirn in ([1, 1, 1], [-1, -1, -1], [1, -1, 0], [0, 0, -1]):
+            pts.append(base)
+            us.append(0.6 * np.array(dirn, dtype=float))
+    box = W.BoxInit(n, n, n, particles=[(np.array(pts), np.array(us), np.full(len(pts), 0.05))], rho_bg=0.0)
+    wl = W.Workload("pcs_edges", W.DT_HALF_COURANT, [W.SpeciesDef("e", -1.0, 1.0, 3)], [box])
+    _one_step_parity(orc, wl, MIXED_TOL, sc=(4, 4, 4), threads_per_sc=128)
+
+
+def test_pcs_diagnostics_match_oracle(orc):
+    require_gpu()
+    wl = _thermal(n=(16, 16, 16), shape=3, u_th=0.1)
+    ctx = ctx_from(wl, sc=(4, 4, 4), threads_per_sc=128)
+    ctx.step(3)
+    st, _ = oracle_state_from_gpu(orc, ctx, wl, 0)
+    got, want = ctx.diagnostics(0), st.diagnostics()
+    assert abs(got[0] / want[0] - 1) < 1e-6 and abs(got[1] / want[1] - 1) < 1e-6
+    assert abs(got[2] - want[2]) < 1e-9 * (1 + abs(want[2]))
+    assert abs(got[3] - want[3]) < 1e-5 * np.max(np.abs(st.rho()))
+    ctx.close()
+
+
+def test_pcs_rejected_where_unsupported():
+    from paper_1606_02862_gb300 import pic
+
+    require_gpu()
+    with pytest.raises(pic.PicError):  # the plain form has CIC and TSC only
+        ctx_from(_thermal(n=(8, 8, 8), shape=3), precision=pic.PRECISION_FP64_PLAIN)
+    with pytest.raises(pic.PicError):  # no PCS kernel for 8x8x4 supercells
+        ctx_from(_thermal(n=(16, 16, 16), shape=3), sc=(8, 8, 4), threads_per_sc=256)
