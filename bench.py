@@ -165,7 +165,7 @@ def make_state(torch, n, ppc, u_th, pinned=True):
     return X, U, Wt
 
 
-SHAPE = {"tsc": 2, "cic": 1}
+SHAPE = {"tsc": 2, "cic": 1, "pcs": 3}
 
 
 GATHER = {"momentum": 0, "energy": 1}
@@ -642,7 +642,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
-    ap.add_argument("--shape", default="tsc", choices=["tsc", "cic"],
+    ap.add_argument("--shape", default="tsc", choices=["tsc", "cic", "pcs"],
                     help="particle shape of the headline thermal workload")
     ap.add_argument("--gather", default="momentum", choices=["momentum", "energy"],
                     help="gather variant of the headline thermal workload")
@@ -651,6 +651,8 @@ def main():
                              "khi_128", "laser_window"])
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.shape == "pcs":
+        args.no_plain = True  # the plain FP64 form has CIC and TSC only
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

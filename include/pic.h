@@ -65,7 +65,7 @@ typedef struct {
  * shape 1 = cloud-in-cell (linear), 2 = triangular-shaped cloud (quadratic
  * spline, the TSC of Sec. 4), 3 = piecewise cubic spline (PCS, beyond the
  * paper; mixed form only, supercells 4x4x4 with 128 threads or 8x4x4 with
- * 256, box edge along x >= 8; a context with a PCS species pads its fields
+ * 256, box edges >= 8; a context with a PCS species pads its fields
  * with 2 guard cells below); mobile = 0 freezes the species (it still
  * counts in the charge density and the diagnostics, and deposits no current).
  * gather: PIC_GATHER_MOMENTUM (0) interpolates every field component with

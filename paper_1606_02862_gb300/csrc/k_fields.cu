@@ -67,18 +67,22 @@ __device__ __forceinline__ CellAt yee_cell(const YeeArgs& a, const BoxDev*& bp)
 }
 
 // Periodic images of an interior coordinate v in [0, n) inside the padded
-// range [-lo, n + hi): v itself, v + n when v < hi, v - n when v >= n - lo
-// (boxes are at least as large as the guards, so no second wrap).  Returns
-// the count (1..3), [0] = v.
+// range [-lo, n + hi): v itself, and v + n when v < hi or v - n when
+// v >= n - lo.  Boxes are at least lo + hi cells long (4 for CIC/TSC
+// guards, 8 with the PCS guards), so at most one of the two applies.
+// Returns the count (1 or 2), [0] = v.
 __device__ __forceinline__ int images(int v, int n, int lo, int hi, int* out)
 {
     out[0] = v;
-    int k = 1;
-    if (v < hi)
-        out[k++] = v + n;
-    if (v >= n - lo)
-        out[k++] = v - n;
-    return k;
+    if (v < hi) {
+        out[1] = v + n;
+        return 2;
+    }
+    if (v >= n - lo) {
+        out[1] = v - n;
+        return 2;
+    }
+    return 1;
 }
 
 __device__ __forceinline__ int images_x(const BoxDev& b, int v, int* out)
@@ -97,7 +101,7 @@ __device__ __forceinline__ int images_z(const BoxDev& b, int v, int* out)
 __device__ __forceinline__ void store_with_images(const BoxDev& b, float* F, const CellAt& c,
                                                   float v)
 {
-    int ix[3], iy[3], iz[3];
+    int ix[2], iy[2], iz[2];
     int nx = images_x(b, c.x, ix), ny = images_y(b, c.y, iy), nz = images_z(b, c.z, iz);
     for (int k = 0; k < nz; ++k)
         for (int j = 0; j < ny; ++j)
@@ -105,6 +109,34 @@ __device__ __forceinline__ void store_with_images(const BoxDev& b, float* F, con
                 F[padded_index(b, ix[i], iy[j], iz[k])] = v;
 }
 
+// The Yee kernels take the guard layout as a template constant (G = 1:
+// CIC/TSC contexts, 2: PCS), so that the image arithmetic of every cell is
+// immediate.
+template <int G>
+struct GuardsOf {
+    static constexpr int hx = G == 1 ? 3 : 6, hyz = G == 1 ? 2 : 3;
+};
+
+template <int G>
+__device__ __forceinline__ int64_t pidx(const BoxDev& b, int x, int y, int z)
+{
+    return ((int64_t)(z + G) * b.py + (y + G)) * b.px + (x + G);
+}
+
+template <int G>
+__device__ __forceinline__ void store_images_g(const BoxDev& b, float* F, const CellAt& c, float v)
+{
+    int ix[2], iy[2], iz[2];
+    const int nx = images(c.x, b.nx, G, GuardsOf<G>::hx, ix);
+    const int ny = images(c.y, b.ny, G, GuardsOf<G>::hyz, iy);
+    const int nz = images(c.z, b.nz, G, GuardsOf<G>::hyz, iz);
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i)
+                F[pidx<G>(b, ix[i], iy[j], iz[k])] = v;
+}
+
+template <int G>
 __global__ void __launch_bounds__(256) k_yee_b(const YeeArgs a)
 {
     const BoxDev* bp;
@@ -114,16 +146,16 @@ __global__ void __launch_bounds__(256) k_yee_b(const YeeArgs a)
     const BoxDev& b = *bp;
     const int64_t pc = padded_cells(b);
     const int64_t sx = 1, sy = b.px, sz = (int64_t)b.px * b.py;
-    const int64_t i = padded_index(b, c.x, c.y, c.z);
+    const int64_t i = pidx<G>(b, c.x, c.y, c.z);
     const float *Ex = b.E, *Ey = b.E + pc, *Ez = b.E + 2 * pc;
     float *Bx = b.B, *By = b.B + pc, *Bz = b.B + 2 * pc;
     const float ex = Ex[i], ey = Ey[i], ez = Ez[i];
     const float cx = (Ez[i + sy] - ez) * a.ih[1] - (Ey[i + sz] - ey) * a.ih[2];
     const float cy = (Ex[i + sz] - ex) * a.ih[2] - (Ez[i + sx] - ez) * a.ih[0];
     const float cz = (Ey[i + sx] - ey) * a.ih[0] - (Ex[i + sy] - ex) * a.ih[1];
-    store_with_images(b, Bx, c, Bx[i] - a.tau * cx);
-    store_with_images(b, By, c, By[i] - a.tau * cy);
-    store_with_images(b, Bz, c, Bz[i] - a.tau * cz);
+    store_images_g<G>(b, Bx, c, Bx[i] - a.tau * cx);
+    store_images_g<G>(b, By, c, By[i] - a.tau * cy);
+    store_images_g<G>(b, Bz, c, Bz[i] - a.tau * cz);
 }
 
 // Laser antenna: adds the sheet current at the Ex positions
@@ -162,6 +194,7 @@ __global__ void __launch_bounds__(256) k_antenna(const YeeArgs a)
     }
 }
 
+template <int G>
 __global__ void __launch_bounds__(256) k_yee_e(const YeeArgs a)
 {
     const BoxDev* bp;
@@ -171,15 +204,17 @@ __global__ void __launch_bounds__(256) k_yee_e(const YeeArgs a)
     const BoxDev& b = *bp;
     const int64_t pc = padded_cells(b);
     const int64_t sx = 1, sy = b.px, sz = (int64_t)b.px * b.py;
-    const int64_t i = padded_index(b, c.x, c.y, c.z);
+    const int64_t i = pidx<G>(b, c.x, c.y, c.z);
     // fold the J guard images into the interior
-    int ix[3], iy[3], iz[3];
-    int nx = images_x(b, c.x, ix), ny = images_y(b, c.y, iy), nz = images_z(b, c.z, iz);
+    int ix[2], iy[2], iz[2];
+    const int nx = images(c.x, b.nx, G, GuardsOf<G>::hx, ix);
+    const int ny = images(c.y, b.ny, G, GuardsOf<G>::hyz, iy);
+    const int nz = images(c.z, b.nz, G, GuardsOf<G>::hyz, iz);
     float jx = 0.f, jy = 0.f, jz = 0.f;
     for (int k = 0; k < nz; ++k)
         for (int j = 0; j < ny; ++j)
             for (int q = 0; q < nx; ++q) {
-                int64_t g = padded_index(b, ix[q], iy[j], iz[k]);
+                int64_t g = pidx<G>(b, ix[q], iy[j], iz[k]);
                 jx += b.J[g];
                 jy += b.J[pc + g];
                 jz += b.J[2 * pc + g];
@@ -198,9 +233,9 @@ __global__ void __launch_bounds__(256) k_yee_e(const YeeArgs a)
     const float cx = (bz - Bz[i - sy]) * a.ih[1] - (by - By[i - sz]) * a.ih[2];
     const float cy = (bx - Bx[i - sz]) * a.ih[2] - (bz - Bz[i - sx]) * a.ih[0];
     const float cz = (by - By[i - sx]) * a.ih[0] - (bx - Bx[i - sy]) * a.ih[1];
-    store_with_images(b, Ex, c, Ex[i] + a.tau * (cx - jx));
-    store_with_images(b, Ey, c, Ey[i] + a.tau * (cy - jy));
-    store_with_images(b, Ez, c, Ez[i] + a.tau * (cz - jz));
+    store_images_g<G>(b, Ex, c, Ex[i] + a.tau * (cx - jx));
+    store_images_g<G>(b, Ey, c, Ey[i] + a.tau * (cy - jy));
+    store_images_g<G>(b, Ez, c, Ez[i] + a.tau * (cz - jz));
 }
 
 // y absorber: every E and B value whose staggered y position lies in a
@@ -259,13 +294,15 @@ cudaError_t launch_yee_mixed_plan(const YeePlan& p, cudaStream_t st)
     YeeArgs a{p.boxes, p.blk_off, p.nboxes, 0.5f * p.dt, {p.ih[0], p.ih[1], p.ih[2]},
               p.step_no, p.dt_d, {p.dx_d[0], p.dx_d[1], p.dx_d[2]}};
     dim3 blk(32, 8);
-    k_yee_b<<<p.nblocks, blk, 0, st>>>(a);
+    auto yb = p.guard == 2 ? k_yee_b<2> : k_yee_b<1>;
+    auto ye = p.guard == 2 ? k_yee_e<2> : k_yee_e<1>;
+    yb<<<p.nblocks, blk, 0, st>>>(a);
     if (p.antenna)
         k_antenna<<<64, 256, 0, st>>>(a);
     a.tau = p.dt;
-    k_yee_e<<<p.nblocks, blk, 0, st>>>(a);
+    ye<<<p.nblocks, blk, 0, st>>>(a);
     a.tau = 0.5f * p.dt;
-    k_yee_b<<<p.nblocks, blk, 0, st>>>(a);
+    yb<<<p.nblocks, blk, 0, st>>>(a);
     if (p.abs_nblocks > 0)
         k_absorb_y<<<p.abs_nblocks, 256, 0, st>>>(p.boxes, p.abs_off, p.nboxes);
     return cudaGetLastError();

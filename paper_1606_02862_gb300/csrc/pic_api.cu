@@ -473,7 +473,7 @@ pic_status enqueue_step_mixed(pic_ctx* c, int parity, cudaEvent_t* ev, bool exte
     YeePlan yp{c->boxes_d, c->yee_off_d, c->nboxes, c->yee_nblocks, (float)c->dt,
                {(float)(1.0 / c->h[0]), (float)(1.0 / c->h[1]), (float)(1.0 / c->h[2])},
                c->step_no, c->dt, {c->h[0], c->h[1], c->h[2]}, c->abs_off_d, c->abs_nblocks,
-               c->any_antenna ? 1 : 0};
+               c->any_antenna ? 1 : 0, c->guard};
     CK(launch_yee_mixed_plan(yp, c->stream));
     if (ev)
         CK(record(ev[3], c->stream, external));
@@ -860,7 +860,7 @@ pic_status pic_create(const pic_grid* grids, int32_t nboxes, const double dx[3],
             const pic_grid& g = grids[b];
             if (g.nx % c->LX || g.ny % c->LY || g.nz % c->LZ)
                 return bail(PIC_ERR_ARG);
-            if (c->guard == 2 && g.nx < 8)  // one periodic image per guard cell
+            if (c->guard == 2 && (g.nx < 8 || g.ny < 8 || g.nz < 8))  // one periodic image per guard cell
                 return bail(PIC_ERR_ARG);
             BoxDev& bd = c->boxes_h[b];
             bd.nx = g.nx;

@@ -167,6 +167,7 @@ struct YeePlan {
     const int* abs_off;        // device [nboxes + 1] block offsets of the y absorber (or null)
     int abs_nblocks;
     int antenna;               // nonzero: some box has an antenna (launch k_antenna)
+    int guard;                 // field guard cells below the interior (1 or 2)
 };
 cudaError_t configure_push(int LX, int LY, int LZ, int threads, int guard, int* per_sm);
 cudaError_t launch_push_deposit(const StepDev& d, int threads, int grid, cudaStream_t st);
