@@ -42,8 +42,9 @@
 //   general: the rest (a few percent of particles) are listed and deposited
 //     with the general 4-node window in a loop of their own, so the rare
 //     case costs no divergence in the common loop.
-// The shared tiles use an odd row pitch so that the 32 banks spread over
-// neighbouring rows.
+// The shared tiles use a row pitch of 4 mod 8 floats, so that rows are
+// 16-byte aligned (the E/B tile arrives by cp.async, the J tile leaves as
+// float4) and the 32 banks spread over neighbouring rows.
 #include "pic_internal.cuh"
 
 #include <cmath>
@@ -67,7 +68,10 @@ struct Tile {
     static constexpr int TX = G == 1 ? LX + 4 : LX + 8;
     static constexpr int TY = G == 1 ? LY + 3 : LY + 5;
     static constexpr int TZ = G == 1 ? LZ + 3 : LZ + 5;
-    static constexpr int PX = TX + 1;  // odd shared-memory row pitch
+    // shared-memory row pitch: the first multiple of 4 at or above TX that is
+    // 4 mod 8, so that rows are 16-byte aligned and consecutive rows start 12
+    // (or 20) banks apart
+    static constexpr int PX = (TX % 8 == 4) ? TX : (TX % 8 == 0 ? TX + 4 : ((TX + 3) / 4) * 4);
     static constexpr int N = PX * TY * TZ;  // shared floats per component
     static constexpr int S = LX * LY * LZ;
 };
@@ -1134,13 +1138,18 @@ __global__ void __launch_bounds__(NT, (T::G == 1 ? 1024 : 512) / NT) k_push_depo
     // between launches, so all CTAs agree)
     const bool sort_pass = d.sort_every <= 1 || (*d.step_ctr % d.sort_every) == 0;
 
+    // work items: tid 0 asks for the next one while the block works on the
+    // current one, and publishes it at the end of the item
+    if (tid == 0)
+        sh.item = atomicAdd(d.work_counter, 1);
+    __syncthreads();
     for (;;) {
-        if (tid == 0)
-            sh.item = atomicAdd(d.work_counter, 1);
-        __syncthreads();
         const int item = sh.item;
         if (item >= d.nsc)
             break;
+        int next_item = 0;
+        if (tid == 0)
+            next_item = atomicAdd(d.work_counter, 1);
         const int g = d.items[item];
         const BoxDev bx = d.boxes[d.sc_box[g]];
         const int loc = g - bx.sc_base;
@@ -1159,6 +1168,8 @@ __global__ void __launch_bounds__(NT, (T::G == 1 ? 1024 : 512) / NT) k_push_depo
         }
         __syncthreads();
         if (sh.any == 0) {
+            if (tid == 0)
+                sh.item = next_item;
             __syncthreads();  // item / any are rewritten next round
             continue;
         }
@@ -1187,16 +1198,11 @@ __global__ void __launch_bounds__(NT, (T::G == 1 ? 1024 : 512) / NT) k_push_depo
             const int tz = (row / TY) % TZ;
             const int c = row / (TY * TZ);
             const float* base = (c < 3 ? bx.E : bx.B) + (c % 3) * pcell;
-            const float4 val = __ldg(reinterpret_cast<const float4*>(
-                                         base + start + ((int64_t)tz * bx.py + ty) * bx.px) + r4);
-            float* dst = sF + row * PX + 4 * r4;
-            dst[0] = val.x;
-            dst[1] = val.y;
-            dst[2] = val.z;
-            dst[3] = val.w;
+            cp_async16(sF + row * PX + 4 * r4, base + start + ((int64_t)tz * bx.py + ty) * bx.px + 4 * r4);
         }
-        for (int v = tid; v < 6 * N; v += NT)
-            sJi[v] = 0;  // int and float current tiles are contiguous; 0 bits = 0.0f
+        for (int v = tid; v < 6 * N / 4; v += NT)  // int and float current tiles, contiguous; 0 bits = 0.0f
+            reinterpret_cast<int4*>(sJi)[v] = make_int4(0, 0, 0, 0);
+        cp_async_wait_all();
         __syncthreads();
 
         // ---- 2. particles of every mobile species, 3. compaction
@@ -1239,8 +1245,7 @@ __global__ void __launch_bounds__(NT, (T::G == 1 ? 1024 : 512) / NT) k_push_depo
         for (int v = tid; v < NJ4; v += NT) {
             const int r4 = v % ROW4;
             const int row = v / ROW4;
-            const float* src = sJf + row * PX + 4 * r4;
-            const float4 val = make_float4(src[0], src[1], src[2], src[3]);
+            const float4 val = *reinterpret_cast<const float4*>(sJf + row * PX + 4 * r4);
             if (val.x != 0.f || val.y != 0.f || val.z != 0.f || val.w != 0.f) {
                 const int ty = row % TY;
                 const int tz = (row / TY) % TZ;
@@ -1249,6 +1254,8 @@ __global__ void __launch_bounds__(NT, (T::G == 1 ? 1024 : 512) / NT) k_push_depo
                 atomicAdd(reinterpret_cast<float4*>(dst), val);
             }
         }
+        if (tid == 0)
+            sh.item = next_item;
         __syncthreads();
     }
     if (my_status)
