@@ -3,16 +3,20 @@
 //
 // One CTA works on one supercell at a time (Sec. 2.1: a supercell maps to a
 // block, its threads share the supercell's particles); CTAs are persistent
-// and pull supercells from a work counter, so boxes of any size and
-// occupancy share one launch.  Per supercell:
-//   1. stage the E and B tile (supercell + 1 guard cell below, 3 (x) / 2
-//      (y, z) above) from HBM into shared memory with 16-byte vector loads;
+// and pull supercells from a work counter (one item ahead), so boxes of any
+// size and occupancy share one launch.  Per supercell:
+//   1. stage the E and B tile (supercell + G guard cells below, G = 1 for
+//      CIC/TSC, 2 with PCS) from HBM into shared memory with 16-byte
+//      asynchronous copies;
 //   2. zero a shared J tile of the same extent;
 //   3. every thread takes particles of the supercell's frame lists: gather
-//      E, B from shared memory (CIC 2x2x2 / TSC 3x3x3 weights per component
-//      at its Yee position, Sec. 4), relativistic Boris push, move, then
-//      Esirkepov deposition (Sec. 4) into the shared J tile with shared
-//      atomics; particles that leave the supercell go to the move buffer;
+//      E, B from shared memory (CIC 2x2x2 / TSC 3x3x3 / PCS 4x4x4 weights
+//      per component at its Yee position, Sec. 4; optionally one order lower
+//      along the component's staggered axes, the energy-conserving variant),
+//      relativistic Boris push, move, then Esirkepov deposition (Sec. 4) into
+//      the shared J tile with shared atomics; particles that leave the
+//      supercell go to the move buffer (or, through a y face of an open-y
+//      box, out of the simulation);
 //   4. compact the frame list (fill the holes the leavers left);
 //   5. add the J tile to the guard-padded global J with 16-byte vector
 //      atomics (neighbouring supercells overlap in their guard cells).
@@ -24,24 +28,26 @@
 // i.e. an outer product of a prefix sum along x and a transverse factor.
 //
 // Particles go through a chunk of at most 256 at a time in the order of a
-// counting sort by nearest node, so the lanes of a warp read neighbouring
-// field words (shared-memory broadcasts).  Every sort_every-th step (a sort
-// pass) stages each chunk in shared memory, sorts it and writes it back to
-// the list in sorted order; the steps between push the lists in stored
-// order, straight from the pool into registers.  The push writes a deposit
-// record per particle; the deposit then runs in a lane order whose
-// neighbours are kDepStride sorted positions apart, so one warp's atomics
-// land on different nodes.  The current of a chunk accumulates in fixed
-// point (see chunk_scale).
-// Two deposit paths, both exact forms of that formula:
-//   common: on every axis the old and the new position round to the same
-//     node (TSC) / stay in the same cell (CIC), so the union of the two
-//     supports is 3 (TSC) / 2 (CIC) nodes and DS has closed per-node forms
-//     in the displacement D (no cancellation in FP32); 54 (TSC) / 12 (CIC)
-//     shared atomics, no branches;
+// counting sort by nearest node (cell for CIC and PCS), so the lanes of a
+// warp read neighbouring field words (shared-memory broadcasts).  Every
+// sort_every-th step (a sort pass) stages each chunk in shared memory, sorts
+// it and writes it back to the list in sorted order; the steps between push
+// the lists in stored order from the chunk stage, which an asynchronous copy
+// fills while the previous chunk deposits.  The push writes a deposit record
+// per particle; the deposit then runs in a lane order whose neighbours are
+// kDepStride sorted positions apart, so one warp's atomics land on different
+// nodes.  The current of a chunk accumulates in fixed point (see
+// chunk_scale).  Two deposit paths, both exact forms of that formula:
+//   common: on every axis the move stays on one spline piece -- the old and
+//     the new position round to the same node (TSC) / stay in the same cell
+//     (CIC, PCS) -- so the union of the two supports is 3 (TSC) / 2 (CIC) /
+//     4 (PCS) nodes and DS has closed per-node forms in the displacement D
+//     (no cancellation in FP32); 54 (TSC) / 12 (CIC) / 144 (PCS) shared
+//     atomics, no branches;
 //   general: the rest (a few percent of particles) are listed and deposited
-//     with the general 4-node window in a loop of their own, so the rare
-//     case costs no divergence in the common loop.
+//     on a 4-node (CIC, TSC) or 5-node (PCS) window after the common loop:
+//     whole groups of 32 lane-parallel, the leftover moves one per warp with
+//     all 32 lanes on the move's current lines.
 // The shared tiles use a row pitch of 4 mod 8 floats, so that rows are
 // 16-byte aligned (the E/B tile arrives by cp.async, the J tile leaves as
 // float4) and the 32 banks spread over neighbouring rows.
@@ -207,13 +213,11 @@ struct AxisW {
     static constexpr int NW = SHAPE == 2 ? 3 : (SHAPE == 3 ? 4 : 2);
     int bi, bh;  // tile index of the first node
     float wi[NW], wh[NW];
-    float di;    // TSC: o - a
     __device__ __forceinline__ AxisW(int l, float o, bool red)
     {
         if (SHAPE == 3) {
             // integer nodes cell-1 .. cell+2; half nodes m0 .. m0+3 with
             // m0 = cell - 2 + up (the half node m + 1/2 is stored at index m)
-            di = o;
             bi = l;
             wi[0] = pcs_S(o + 1.0f);
             wi[1] = pcs_S(o);
@@ -235,7 +239,7 @@ struct AxisW {
             }
         } else if (SHAPE == 2) {
             bool up = o >= 0.5f;
-            di = up ? o - 1.0f : o;
+            const float di = up ? o - 1.0f : o;  // offset from the nearest node
             bi = l + (up ? 1 : 0);
             float a = 0.5f - di, c = 0.5f + di;
             wi[0] = 0.5f * a * a;
@@ -254,7 +258,6 @@ struct AxisW {
                 wh[2] = 0.5f * ch * ch;
             }
         } else {
-            di = o;
             bi = l + 1;
             wi[0] = 1.0f - o;
             wi[1] = o;
@@ -697,20 +700,6 @@ struct Part {
     int cell;
     float o[3], u[3], w;
 };
-
-__device__ __forceinline__ Part load_part(const StepDev& d, int64_t idx)
-{
-    Part q;
-    q.cell = d.cell[idx];
-    q.o[0] = d.ox[idx];
-    q.o[1] = d.oy[idx];
-    q.o[2] = d.oz[idx];
-    q.u[0] = d.ux[idx];
-    q.u[1] = d.uy[idx];
-    q.u[2] = d.uz[idx];
-    q.w = d.w[idx];
-    return q;
-}
 
 // Writes a pushed particle to pool slot idx (only the cell of a leaver);
 // the weight only when the particle changed slot.
