@@ -22,6 +22,8 @@
 
 namespace pic {
 
+constexpr int kYeeZ = kYeeCellsZ;  // box edges are multiples of the supercell edge, >= 4
+
 struct YeeArgs {
     const BoxDev* boxes;
     const int* blk_off;  // [nboxes + 1]
@@ -136,6 +138,9 @@ __device__ __forceinline__ void store_images_g(const BoxDev& b, float* F, const 
                 F[pidx<G>(b, ix[i], iy[j], iz[k])] = v;
 }
 
+// Each thread updates kYeeZ cells stacked in z: all loads first, then the
+// arithmetic and the stores, so that a warp keeps kYeeZ times the bytes in
+// flight (the update is bound by DRAM latency with one cell per thread).
 template <int G>
 __global__ void __launch_bounds__(256) k_yee_b(const YeeArgs a)
 {
@@ -146,16 +151,32 @@ __global__ void __launch_bounds__(256) k_yee_b(const YeeArgs a)
     const BoxDev& b = *bp;
     const int64_t pc = padded_cells(b);
     const int64_t sx = 1, sy = b.px, sz = (int64_t)b.px * b.py;
-    const int64_t i = pidx<G>(b, c.x, c.y, c.z);
-    const float *Ex = b.E, *Ey = b.E + pc, *Ez = b.E + 2 * pc;
-    float *Bx = b.B, *By = b.B + pc, *Bz = b.B + 2 * pc;
-    const float ex = Ex[i], ey = Ey[i], ez = Ez[i];
-    const float cx = (Ez[i + sy] - ez) * a.ih[1] - (Ey[i + sz] - ey) * a.ih[2];
-    const float cy = (Ex[i + sz] - ex) * a.ih[2] - (Ez[i + sx] - ez) * a.ih[0];
-    const float cz = (Ey[i + sx] - ey) * a.ih[0] - (Ex[i + sy] - ex) * a.ih[1];
-    store_images_g<G>(b, Bx, c, Bx[i] - a.tau * cx);
-    store_images_g<G>(b, By, c, By[i] - a.tau * cy);
-    store_images_g<G>(b, Bz, c, Bz[i] - a.tau * cz);
+    const float* __restrict__ Ex = b.E;
+    const float* __restrict__ Ey = b.E + pc;
+    const float* __restrict__ Ez = b.E + 2 * pc;
+    float* __restrict__ Bx = b.B;
+    float* __restrict__ By = b.B + pc;
+    float* __restrict__ Bz = b.B + 2 * pc;
+    const int z0 = c.z * kYeeZ;
+    float cx[kYeeZ], cy[kYeeZ], cz[kYeeZ], bx[kYeeZ], by[kYeeZ], bz[kYeeZ];
+#pragma unroll
+    for (int q = 0; q < kYeeZ; ++q) {
+        const int64_t i = pidx<G>(b, c.x, c.y, z0 + q);
+        const float ex = __ldg(Ex + i), ey = __ldg(Ey + i), ez = __ldg(Ez + i);
+        cx[q] = (__ldg(Ez + i + sy) - ez) * a.ih[1] - (__ldg(Ey + i + sz) - ey) * a.ih[2];
+        cy[q] = (__ldg(Ex + i + sz) - ex) * a.ih[2] - (__ldg(Ez + i + sx) - ez) * a.ih[0];
+        cz[q] = (__ldg(Ey + i + sx) - ey) * a.ih[0] - (__ldg(Ex + i + sy) - ex) * a.ih[1];
+        bx[q] = Bx[i];
+        by[q] = By[i];
+        bz[q] = Bz[i];
+    }
+#pragma unroll
+    for (int q = 0; q < kYeeZ; ++q) {
+        c.z = z0 + q;
+        store_images_g<G>(b, Bx, c, bx[q] - a.tau * cx[q]);
+        store_images_g<G>(b, By, c, by[q] - a.tau * cy[q]);
+        store_images_g<G>(b, Bz, c, bz[q] - a.tau * cz[q]);
+    }
 }
 
 // Laser antenna: adds the sheet current at the Ex positions
@@ -195,7 +216,7 @@ __global__ void __launch_bounds__(256) k_antenna(const YeeArgs a)
 }
 
 template <int G>
-__global__ void __launch_bounds__(256) k_yee_e(const YeeArgs a)
+__global__ void __launch_bounds__(256, 4) k_yee_e(const YeeArgs a)
 {
     const BoxDev* bp;
     CellAt c = yee_cell(a, bp);
@@ -204,38 +225,73 @@ __global__ void __launch_bounds__(256) k_yee_e(const YeeArgs a)
     const BoxDev& b = *bp;
     const int64_t pc = padded_cells(b);
     const int64_t sx = 1, sy = b.px, sz = (int64_t)b.px * b.py;
-    const int64_t i = pidx<G>(b, c.x, c.y, c.z);
-    // fold the J guard images into the interior
-    int ix[2], iy[2], iz[2];
+    const float* __restrict__ Bx = b.B;
+    const float* __restrict__ By = b.B + pc;
+    const float* __restrict__ Bz = b.B + 2 * pc;
+    float* __restrict__ Ex = b.E;
+    float* __restrict__ Ey = b.E + pc;
+    float* __restrict__ Ez = b.E + 2 * pc;
+    float* __restrict__ J = b.J;
+    const int z0 = c.z * kYeeZ;
+    int ix[2], iy[2];
     const int nx = images(c.x, b.nx, G, GuardsOf<G>::hx, ix);
     const int ny = images(c.y, b.ny, G, GuardsOf<G>::hyz, iy);
-    const int nz = images(c.z, b.nz, G, GuardsOf<G>::hyz, iz);
-    float jx = 0.f, jy = 0.f, jz = 0.f;
-    for (int k = 0; k < nz; ++k)
-        for (int j = 0; j < ny; ++j)
-            for (int q = 0; q < nx; ++q) {
-                int64_t g = pidx<G>(b, ix[q], iy[j], iz[k]);
-                jx += b.J[g];
-                jy += b.J[pc + g];
-                jz += b.J[2 * pc + g];
-                if (g != i) {
-                    b.J[g] = 0.f;
-                    b.J[pc + g] = 0.f;
-                    b.J[2 * pc + g] = 0.f;
-                }
-            }
-    b.J[i] = jx;
-    b.J[pc + i] = jy;
-    b.J[2 * pc + i] = jz;
-    const float *Bx = b.B, *By = b.B + pc, *Bz = b.B + 2 * pc;
-    float *Ex = b.E, *Ey = b.E + pc, *Ez = b.E + 2 * pc;
-    const float bx = Bx[i], by = By[i], bz = Bz[i];
-    const float cx = (bz - Bz[i - sy]) * a.ih[1] - (by - By[i - sz]) * a.ih[2];
-    const float cy = (bx - Bx[i - sz]) * a.ih[2] - (bz - Bz[i - sx]) * a.ih[0];
-    const float cz = (by - By[i - sx]) * a.ih[0] - (bx - Bx[i - sy]) * a.ih[1];
-    store_images_g<G>(b, Ex, c, Ex[i] + a.tau * (cx - jx));
-    store_images_g<G>(b, Ey, c, Ey[i] + a.tau * (cy - jy));
-    store_images_g<G>(b, Ez, c, Ez[i] + a.tau * (cz - jz));
+    float jx[kYeeZ], jy[kYeeZ], jz[kYeeZ], cx[kYeeZ], cy[kYeeZ], cz[kYeeZ], ex[kYeeZ], ey[kYeeZ], ez[kYeeZ];
+#pragma unroll
+    for (int q = 0; q < kYeeZ; ++q) {
+        const int64_t i = pidx<G>(b, c.x, c.y, z0 + q);
+        int iz[2];
+        const int nz = images(z0 + q, b.nz, G, GuardsOf<G>::hyz, iz);
+        // fold the J guard images into the interior
+        jx[q] = 0.f;
+        jy[q] = 0.f;
+        jz[q] = 0.f;
+#pragma unroll
+        for (int k = 0; k < 2; ++k)
+#pragma unroll
+            for (int j = 0; j < 2; ++j)
+#pragma unroll
+                for (int r = 0; r < 2; ++r)
+                    if (k < nz && j < ny && r < nx) {
+                        const int64_t g = pidx<G>(b, ix[r], iy[j], iz[k]);
+                        jx[q] += J[g];
+                        jy[q] += J[pc + g];
+                        jz[q] += J[2 * pc + g];
+                    }
+        const float bxv = __ldg(Bx + i), byv = __ldg(By + i), bzv = __ldg(Bz + i);
+        cx[q] = (bzv - __ldg(Bz + i - sy)) * a.ih[1] - (byv - __ldg(By + i - sz)) * a.ih[2];
+        cy[q] = (bxv - __ldg(Bx + i - sz)) * a.ih[2] - (bzv - __ldg(Bz + i - sx)) * a.ih[0];
+        cz[q] = (byv - __ldg(By + i - sx)) * a.ih[0] - (bxv - __ldg(Bx + i - sy)) * a.ih[1];
+        ex[q] = Ex[i];
+        ey[q] = Ey[i];
+        ez[q] = Ez[i];
+    }
+#pragma unroll
+    for (int q = 0; q < kYeeZ; ++q) {
+        const int64_t i = pidx<G>(b, c.x, c.y, z0 + q);
+        int iz[2];
+        const int nz = images(z0 + q, b.nz, G, GuardsOf<G>::hyz, iz);
+        // folded J stays in the interior (read back as the step's current), images cleared
+#pragma unroll
+        for (int k = 0; k < 2; ++k)
+#pragma unroll
+            for (int j = 0; j < 2; ++j)
+#pragma unroll
+                for (int r = 0; r < 2; ++r)
+                    if (k < nz && j < ny && r < nx && (k | j | r) != 0) {
+                        const int64_t g = pidx<G>(b, ix[r], iy[j], iz[k]);
+                        J[g] = 0.f;
+                        J[pc + g] = 0.f;
+                        J[2 * pc + g] = 0.f;
+                    }
+        J[i] = jx[q];
+        J[pc + i] = jy[q];
+        J[2 * pc + i] = jz[q];
+        c.z = z0 + q;
+        store_images_g<G>(b, Ex, c, ex[q] + a.tau * (cx[q] - jx[q]));
+        store_images_g<G>(b, Ey, c, ey[q] + a.tau * (cy[q] - jy[q]));
+        store_images_g<G>(b, Ez, c, ez[q] + a.tau * (cz[q] - jz[q]));
+    }
 }
 
 // y absorber: every E and B value whose staggered y position lies in a

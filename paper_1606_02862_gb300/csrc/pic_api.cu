@@ -881,7 +881,7 @@ pic_status pic_create(const pic_grid* grids, int32_t nboxes, const double dx[3],
             bd.oy.ant_j = -1;
             nsc += bd.nscx * bd.nscy * bd.nscz;
             floats += 3 * padded_cells(bd);
-            yee_off[b + 1] = yee_off[b] + ((g.nx + 31) / 32) * ((g.ny + 7) / 8) * g.nz;
+            yee_off[b + 1] = yee_off[b] + ((g.nx + 31) / 32) * ((g.ny + 7) / 8) * (g.nz / kYeeCellsZ);
         }
         c->nsc = nsc;
         c->nlists = nsc * nspecies;

@@ -35,6 +35,7 @@ namespace pic {
 
 constexpr int kMaxSpecies = 8;
 constexpr int kDefaultSortEvery = 4;  // steps between sort passes of the push (mixed form)
+constexpr int kYeeCellsZ = 4;         // cells per thread along z in the Yee kernels
 
 // Device status word bits (OR-ed by kernels, read by the host after a step).
 enum : unsigned {
