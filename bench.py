@@ -521,6 +521,47 @@ def run_workload(args):
                if plain else {})}
 
 
+def run_yee(args):
+    """The field update alone (scope row a5): an n^3 box without particles,
+    random E, stage events around the B half, E, B half launches of each step.
+    Rate in cell updates/s; roofline against 132 B/cell of algorithmic DRAM
+    traffic (B half: E, B read and B written, 36 B; E: B, E, J read, E, J
+    written, 60 B)."""
+    import torch
+
+    from paper_1606_02862_gb300 import build as libbuild
+    from paper_1606_02862_gb300 import pic
+    from paper_1606_02862_gb300 import workloads as W
+
+    libbuild.build()
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    n = args.n
+    ctx = pic.Context([(n, n, n)], (1.0, 1.0, 1.0), W.DT_HALF_COURANT, [pic.Species(-1.0, 1.0, 2, True)],
+                      sc=(8, 4, 4), threads_per_sc=256, use_graph=True)
+    rng = np.random.default_rng(W.BASE_SEED + 7)
+    ctx.write_fields(0, pic.FIELD_E, rng.normal(0.0, 0.01, (3, n, n, n)))
+    ctx.step(args.warmup)
+    ctx.stage_timing(True)
+    ctx.step(args.steps)
+    ms, nst = ctx.stage_times()
+    ctx.close()
+    yee_ms = ms[2] / nst
+    cells = n ** 3
+    hbm, hbm_src = measured_hbm()
+    achieved = 132.0 * cells / (yee_ms * 1e-3) / 1e9
+    return {"metric": "cell updates/sec of the Yee field update (B half, E, B half) at 1 GB300",
+            "value": cells / (yee_ms * 1e-3), "unit": "cell updates/s", "n_gpus": 1, "steps": nst,
+            "warmup": args.warmup, "ms_per_step": ms[3] / nst, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"yee_{n}: {n}^3 periodic cells, fields only (random E), FP32, guard-padded",
+                       "l2": "fields larger than L2" if 9 * 4 * cells > 129e6 else "fields fit in L2"},
+            "stage_ms_per_step": {"yee": yee_ms},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm, "traffic": None, "kernel": "k_yee_b, k_yee_e",
+                         "peak_source": hbm_src, "bytes_per_cell": 132}}
+
+
 def run_window(args):
     """The open-boundary laser workload with a moving window: push+deposit
     rate from the in-graph stage events (steps only), and the whole cycle per
@@ -648,7 +689,7 @@ def main():
                     help="gather variant of the headline thermal workload")
     ap.add_argument("--workload", default="thermal_tsc_256",
                     choices=["thermal_tsc_256", "small_cic_32", "laser_ramp", "foil_overdense",
-                             "khi_128", "laser_window"])
+                             "khi_128", "laser_window", "yee"])
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.shape == "pcs":
@@ -666,6 +707,8 @@ def main():
         line = run_reference(args, rank)
     elif args.workload == "laser_window":
         line = run_window(args) if rank == 0 else None
+    elif args.workload == "yee":
+        line = run_yee(args) if rank == 0 else None
     elif args.workload != "thermal_tsc_256":
         line = run_workload(args) if rank == 0 else None
     else:
