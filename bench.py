@@ -61,9 +61,11 @@ def measured_hbm():
 
 
 def push_profile():
-    """Per-particle DRAM bytes and shared-memory wavefronts of the push kernel
-    from the committed ncu summary, or Nones when the summary is absent or the
-    kernel source changed since the counters were taken."""
+    """Per-particle DRAM bytes, shared-memory wavefronts and FP32 thread
+    instructions of the push kernel from the committed ncu summary (thermal
+    TSC, 8x4x4 supercells, 256 threads), or Nones when the summary is absent or
+    the kernel source changed since the counters were taken."""
+    none = {"tpp": None, "wpp": None, "fpp": None}
     try:
         with open(PUSH_KERNEL_SRC, "rb") as f:
             sha = hashlib.sha256(f.read()).hexdigest()
@@ -74,10 +76,12 @@ def push_profile():
                     k, v = line.strip()[2:].split(":", 1)
                     vals[k.strip()] = v.strip().strip("`")
         if vals.get("k_push.cu sha256") != sha:
-            return None, None
-        return float(vals["dram bytes per particle"]), float(vals["shared wavefronts per particle"])
+            return none
+        return {"tpp": float(vals["dram bytes per particle"]), "wpp": float(vals["shared wavefronts per particle"]),
+                "fpp": float(vals["fp32 instructions per particle"]) if "fp32 instructions per particle" in vals
+                else None}
     except Exception:  # noqa: BLE001
-        return None, None
+        return none
 
 
 class ClockSampler:
@@ -153,6 +157,27 @@ def binding_roofline(result, npart):
     return {"bound": "smem", "achieved": achieved, "peak": peak, "unit": "G wavefronts/s",
             "frac": achieved / peak, "kernel": "k_push_deposit",
             "per_particle": wpp, "peak_source": f"1 wavefront/clk/SM x {nsm} SMs x {mhz:.0f} MHz sampled"}
+
+def alu_roofline(result, npart):
+    """The FP32 arithmetic bound of the push kernel: FFMA + FMUL + FADD thread
+    instructions per particle (ncu, committed profile) per second against 128
+    FP32 lanes per SM per cycle at the sampled SM clock."""
+    fpp = result.get("fpp")
+    mhz = (result.get("clocks") or {}).get("sm_mhz")
+    if not fpp or not mhz:
+        return None
+    try:
+        import torch
+
+        nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    except Exception:  # noqa: BLE001
+        return None
+    achieved = fpp * npart / (result["push_ms"] * 1e-3) / 1e12
+    peak = nsm * 128 * mhz * 1e6 / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "T FP32 thread instructions/s",
+            "frac": achieved / peak, "kernel": "k_push_deposit", "per_particle": fpp,
+            "peak_source": f"128 FP32 lanes/clk/SM x {nsm} SMs x {mhz:.0f} MHz sampled"}
+
 
 def make_state(torch, n, ppc, u_th, pinned=True):
     from paper_1606_02862_gb300 import workloads as W
@@ -356,10 +381,14 @@ def run_ours(args, rank, world, dist):
     value = world * npart / (pd_ms_max * 1e-3)
     push_bytes = npart * MIXED_BYTES_PER_PARTICLE + ncell * MIXED_BYTES_PER_CELL
     achieved = push_bytes / (push_ms * 1e-3) / 1e9
-    tpp, wpp = push_profile()
+    # the committed counters hold for the configuration they were taken on
+    prof = push_profile() if (args.shape == "tsc" and args.gather == "momentum" and tuple(sc) == (8, 4, 4)
+                              and threads in (0, 256)) else {"tpp": None, "wpp": None, "fpp": None}
+    tpp = prof["tpp"]
     result.update(value=value, step_ms=step_ms_max, push_ms=push_ms, frames_ms=frames_ms,
                   yee_ms=yee_ms, graph=graph, kernels=kernels, achieved=achieved,
-                  traffic=None if tpp is None else tpp * npart, clocks=clk.summary(), wpp=wpp)
+                  traffic=None if tpp is None else tpp * npart, clocks=clk.summary(), wpp=prof["wpp"],
+                  fpp=prof["fpp"])
     log(f"[rank {rank}] mixed: push {push_ms:.3f} ms, frames {frames_ms:.3f} ms, yee {yee_ms:.3f} ms,"
         f" step {step_ms:.3f} ms, graph={graph}")
 
@@ -438,6 +467,7 @@ def run_ours(args, rank, world, dist):
                      "kernel": "k_push_deposit", "peak_source": hbm_src,
                      "bytes_per_launch": npart * MIXED_BYTES_PER_PARTICLE + ncell * MIXED_BYTES_PER_CELL},
         "binding": binding_roofline(result, npart),
+        "alu": alu_roofline(result, npart),
         "gpu_launches": int(result["kernels"] * args.steps),
         "clocks": result["clocks"],
     }
