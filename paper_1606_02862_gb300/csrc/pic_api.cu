@@ -1062,7 +1062,7 @@ pic_status pic_load_particles(pic_ctx* c, int32_t box, int32_t species, int64_t 
         return fail(c, PIC_ERR_ARG, "more than 2^31 particles in one (box, species)");
     // captured step graphs stay valid unless a buffer they use is reallocated
     // (ensure_pool / ensure_mv drop them) or a weight bound grows (below)
-    const int64_t chunk = std::min<int64_t>(n, 1 << 22);
+    const int64_t chunk = std::min<int64_t>(n, 1 << 25);  // 32 M particles: 1.9 GB of FP64 staging
     CKS(ensure_stage(c, sizeof(double) * 7 * (size_t)chunk));
     double* sx = static_cast<double*>(c->stage_d);
     double* su = sx + 3 * chunk;
