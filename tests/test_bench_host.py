@@ -1,0 +1,60 @@
+"""Host logic of bench.py (no GPU): the committed push-kernel profile is
+read only while the kernel source still has the hash it was taken on, and
+its per-particle figures parse."""
+import hashlib
+import os
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _bench():
+    import sys
+
+    if ROOT not in sys.path:
+        sys.path.insert(0, ROOT)
+    import bench
+
+    return bench
+
+
+def test_committed_profile_has_every_figure():
+    bench = _bench()
+    vals = {}
+    with open(bench.TRAFFIC_SUMMARY) as f:
+        for line in f:
+            if ":" in line and line.strip().startswith("- "):
+                k, v = line.strip()[2:].split(":", 1)
+                vals[k.strip()] = v.strip().strip("`")
+    assert len(vals["k_push.cu sha256"]) == 64
+    assert 60.0 < float(vals["dram bytes per particle"]) < 80.0   # 64.5 B algorithmic
+    assert 5.0 < float(vals["shared wavefronts per particle"]) < 40.0
+    assert 100.0 < float(vals["fp32 instructions per particle"]) < 3000.0
+
+
+def test_profile_is_used_only_for_the_kernel_it_was_taken_on(tmp_path, monkeypatch):
+    bench = _bench()
+    src = tmp_path / "k_push.cu"
+    src.write_bytes(b"// a kernel\n")
+    sha = hashlib.sha256(src.read_bytes()).hexdigest()
+    md = tmp_path / "profile.md"
+    md.write_text(f"- k_push.cu sha256: `{sha}`\n- dram bytes per particle: `64.5`\n"
+                  f"- shared wavefronts per particle: `17.0`\n- fp32 instructions per particle: `670`\n")
+    monkeypatch.setattr(bench, "PUSH_KERNEL_SRC", str(src))
+    monkeypatch.setattr(bench, "TRAFFIC_SUMMARY", str(md))
+    assert bench.push_profile() == {"tpp": 64.5, "wpp": 17.0, "fpp": 670.0}
+    src.write_bytes(b"// a changed kernel\n")
+    assert bench.push_profile() == {"tpp": None, "wpp": None, "fpp": None}
+
+
+def test_missing_profile_gives_nones(tmp_path, monkeypatch):
+    bench = _bench()
+    monkeypatch.setattr(bench, "TRAFFIC_SUMMARY", str(tmp_path / "absent.md"))
+    assert bench.push_profile() == {"tpp": None, "wpp": None, "fpp": None}
+
+
+@pytest.mark.parametrize("shape", ["tsc", "cic", "pcs"])
+def test_shape_table(shape):
+    bench = _bench()
+    assert bench.SHAPE[shape] in (1, 2, 3)
