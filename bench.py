@@ -401,11 +401,16 @@ def run_ours(args, rank, world, dist):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         ctx = new_ctx(pic, n, pic.PRECISION_MIXED, sc, args.threads, SHAPE[args.shape], GATHER[args.gather])
+        t1 = time.perf_counter()
         load(ctx, X, U, Wt)
+        t2 = time.perf_counter()
         ctx.step(args.steps)
+        t3 = time.perf_counter()
         nout = ctx.read_particles_ptr(0, 0, npart, Xo.data_ptr(), Uo.data_ptr(), Wo.data_ptr())
         ctx.read_fields_ptr(0, pic.FIELD_E, Eo.ctypes.data)
         t_e2e = time.perf_counter() - t0
+        log(f"[rank {rank}] e2e phases: create {t1 - t0:.3f} s, load {t2 - t1:.3f} s, "
+            f"{args.steps} steps {t3 - t2:.3f} s, read back {t0 + t_e2e - t3:.3f} s")
         ctx.close()
         h2d = npart * 56.0
         d2h = nout * 56.0 + Eo.nbytes
