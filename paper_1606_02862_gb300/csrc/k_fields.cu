@@ -10,12 +10,13 @@
 //   B^{n+1}   = B^{n+1/2} - dt/2 curl E^{n+1}
 // Every kernel writes each updated interior value also into its periodic
 // guard images, so the next kernel (and the next push's tile loads) read
-// guards without a separate exchange.  The E kernel first folds the J guard
-// images (deposits that spilled over the periodic seam) into the interior,
-// leaves the folded J in the interior and zeroes the guards.
+// guards without a separate exchange.  The E kernel folds the J guard
+// images (deposits that spilled over the periodic seam) into the current of
+// each interior cell as it reads it; J itself stays as deposited (the step
+// zeroes it before the push, and a read of J folds the same way).
 //
-// One launch covers all boxes: blocks of 32 x 8 cells in x-y, one z layer,
-// box found from a per-box block offset table.
+// One launch covers all boxes: blocks of 32 x 8 cells in x-y, each thread
+// kYeeZ cells along z, box found from a per-box block offset table.
 #include "pic_internal.cuh"
 
 #include <cmath>
@@ -231,7 +232,7 @@ __global__ void __launch_bounds__(256, 4) k_yee_e(const YeeArgs a)
     float* __restrict__ Ex = b.E;
     float* __restrict__ Ey = b.E + pc;
     float* __restrict__ Ez = b.E + 2 * pc;
-    float* __restrict__ J = b.J;
+    const float* __restrict__ J = b.J;
     const int z0 = c.z * kYeeZ;
     int ix[2], iy[2];
     const int nx = images(c.x, b.nx, G, GuardsOf<G>::hx, ix);
@@ -268,25 +269,8 @@ __global__ void __launch_bounds__(256, 4) k_yee_e(const YeeArgs a)
     }
 #pragma unroll
     for (int q = 0; q < kYeeZ; ++q) {
-        const int64_t i = pidx<G>(b, c.x, c.y, z0 + q);
-        int iz[2];
-        const int nz = images(z0 + q, b.nz, G, GuardsOf<G>::hyz, iz);
-        // folded J stays in the interior (read back as the step's current), images cleared
-#pragma unroll
-        for (int k = 0; k < 2; ++k)
-#pragma unroll
-            for (int j = 0; j < 2; ++j)
-#pragma unroll
-                for (int r = 0; r < 2; ++r)
-                    if (k < nz && j < ny && r < nx && (k | j | r) != 0) {
-                        const int64_t g = pidx<G>(b, ix[r], iy[j], iz[k]);
-                        J[g] = 0.f;
-                        J[pc + g] = 0.f;
-                        J[2 * pc + g] = 0.f;
-                    }
-        J[i] = jx[q];
-        J[pc + i] = jy[q];
-        J[2 * pc + i] = jz[q];
+        // J is left as deposited (the step zeroes it before the push, and a
+        // read of J folds the images the same way)
         c.z = z0 + q;
         store_images_g<G>(b, Ex, c, ex[q] + a.tau * (cx[q] - jx[q]));
         store_images_g<G>(b, Ey, c, ey[q] + a.tau * (cy[q] - jy[q]));
@@ -411,7 +395,9 @@ __global__ void k_fields_to_padded(const BoxDev b, float* F, const double* src)
     }
 }
 
-__global__ void k_fields_from_padded(const BoxDev b, const float* F, double* dst)
+// fold: sum the periodic images (the current, whose guards hold deposits
+// that crossed the seam), in the order of the E update's fold.
+__global__ void k_fields_from_padded(const BoxDev b, const float* F, double* dst, int fold)
 {
     const int64_t n = (int64_t)b.nx * b.ny * b.nz;
     const int64_t pc = padded_cells(b);
@@ -420,7 +406,19 @@ __global__ void k_fields_from_padded(const BoxDev b, const float* F, double* dst
         int comp = (int)(t / n);
         int64_t r = t - comp * n;
         int x = (int)(r % b.nx), y = (int)((r / b.nx) % b.ny), z = (int)(r / ((int64_t)b.nx * b.ny));
-        dst[t] = (double)F[comp * pc + padded_index(b, x, y, z)];
+        const float* Fc = F + comp * pc;
+        if (!fold) {
+            dst[t] = (double)Fc[padded_index(b, x, y, z)];
+            continue;
+        }
+        int ix[2], iy[2], iz[2];
+        const int nx = images_x(b, x, ix), ny = images_y(b, y, iy), nz = images_z(b, z, iz);
+        float v = 0.0f;
+        for (int k = 0; k < nz; ++k)
+            for (int j = 0; j < ny; ++j)
+                for (int q = 0; q < nx; ++q)
+                    v += Fc[padded_index(b, ix[q], iy[j], iz[k])];
+        dst[t] = (double)v;
     }
 }
 
@@ -434,7 +432,7 @@ cudaError_t launch_fields_to_padded(const BoxDev& b, int which, const double* sr
 cudaError_t launch_fields_from_padded(const BoxDev& b, int which, double* dst, cudaStream_t st)
 {
     const float* F = which == 0 ? b.E : (which == 1 ? b.B : b.J);
-    k_fields_from_padded<<<1024, 256, 0, st>>>(b, F, dst);
+    k_fields_from_padded<<<1024, 256, 0, st>>>(b, F, dst, which == 2);
     return cudaGetLastError();
 }
 
