@@ -78,7 +78,7 @@ def push_profile():
         if vals.get("k_push.cu sha256") != sha:
             return none
         return {"tpp": float(vals["dram bytes per particle"]), "wpp": float(vals["shared wavefronts per particle"]),
-                "fpp": float(vals["fp32 instructions per particle"]) if "fp32 instructions per particle" in vals
+                "fpp": float(vals["fp32 operations per particle"]) if "fp32 operations per particle" in vals
                 else None}
     except Exception:  # noqa: BLE001
         return none
@@ -159,9 +159,10 @@ def binding_roofline(result, npart):
             "per_particle": wpp, "peak_source": f"1 wavefront/clk/SM x {nsm} SMs x {mhz:.0f} MHz sampled"}
 
 def alu_roofline(result, npart):
-    """The FP32 arithmetic bound of the push kernel: FFMA + FMUL + FADD thread
-    instructions per particle (ncu, committed profile) per second against 128
-    FP32 lanes per SM per cycle at the sampled SM clock."""
+    """The FP32 arithmetic bound of the push kernel: FP32 operations (FFMA,
+    FMUL, FADD; a packed f32x2 instruction counts two) per particle (ncu,
+    committed profile) per second against 128 FP32 lanes per SM per cycle at
+    the sampled SM clock."""
     fpp = result.get("fpp")
     mhz = (result.get("clocks") or {}).get("sm_mhz")
     if not fpp or not mhz:
@@ -174,7 +175,7 @@ def alu_roofline(result, npart):
         return None
     achieved = fpp * npart / (result["push_ms"] * 1e-3) / 1e12
     peak = nsm * 128 * mhz * 1e6 / 1e12
-    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "T FP32 thread instructions/s",
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "T FP32 operations/s",
             "frac": achieved / peak, "kernel": "k_push_deposit", "per_particle": fpp,
             "peak_source": f"128 FP32 lanes/clk/SM x {nsm} SMs x {mhz:.0f} MHz sampled"}
 

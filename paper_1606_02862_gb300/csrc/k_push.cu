@@ -290,6 +290,32 @@ __device__ __forceinline__ float gather_comp(const float* __restrict__ F, int bx
     return acc;
 }
 
+// Two components at once on the packed FP32 pipe (two independent FMAs per
+// instruction, each rounded as the scalar fmaf: the same result as two
+// gather_comp calls).
+template <int NW, int PX, int TY>
+__device__ __forceinline__ float2 gather_pair(const float* __restrict__ F1, int x1, int y1, int z1,
+                                              const float* wx1, const float* wy1, const float* wz1,
+                                              const float* __restrict__ F2, int x2, int y2, int z2,
+                                              const float* wx2, const float* wy2, const float* wz2)
+{
+    float2 acc = make_float2(0.0f, 0.0f);
+#pragma unroll
+    for (int c = 0; c < NW; ++c) {
+#pragma unroll
+        for (int b = 0; b < NW; ++b) {
+            const float* r1 = F1 + ((z1 + c) * TY + (y1 + b)) * PX + x1;
+            const float* r2 = F2 + ((z2 + c) * TY + (y2 + b)) * PX + x2;
+            float2 r = make_float2(0.0f, 0.0f);
+#pragma unroll
+            for (int a = 0; a < NW; ++a)
+                r = __ffma2_rn(make_float2(r1[a], r2[a]), make_float2(wx1[a], wx2[a]), r);
+            acc = __ffma2_rn(r, __fmul2_rn(make_float2(wy1[b], wy2[b]), make_float2(wz1[c], wz2[c])), acc);
+        }
+    }
+    return acc;
+}
+
 // Esirkepov transverse factor S0e S0f + (DSe S0f + S0e DSf)/2 + DSe DSf / 3.
 __device__ __forceinline__ float esk_T(float s0e, float dse, float s0f, float dsf)
 {
@@ -326,10 +352,39 @@ __device__ __forceinline__ float chunk_scale(int n, float bound, float* inv)
     return ldexpf(1.0f, hb - e);
 }
 
+// Esirkepov factor of two lines at once (packed FP32; per lane the same
+// operations as esk_T).
+__device__ __forceinline__ float2 esk_T2(float2 s0e, float2 dse, float2 s0f, float2 dsf)
+{
+    const float2 half = make_float2(0.5f, 0.5f), third = make_float2(1.0f / 3.0f, 1.0f / 3.0f);
+    return __ffma2_rn(s0e, s0f,
+                      __ffma2_rn(half, __ffma2_rn(dse, s0f, __fmul2_rn(s0e, dsf)),
+                                 __fmul2_rn(__fmul2_rn(third, dse), dsf)));
+}
+
+__device__ __forceinline__ float2 dup2(float v) { return make_float2(v, v); }
+
+// One window line pair: the M - 1 terms P[i] T of two parallel lines (tile
+// words a0 + i st and a1 + i st), converted to fixed point two at a time.
+template <int M>
+__device__ __forceinline__ void add_line_pair(int* a0, int* a1, int st, const float* P, float2 T)
+{
+    const float2 magic = dup2(12582912.0f);
+#pragma unroll
+    for (int i = 0; i < M - 1; ++i) {
+        const float2 v = __ffma2_rn(dup2(P[i]), T, magic);
+        atomicAdd(a0 + i * st, __float_as_int(v.x) - 0x4B400000);
+        atomicAdd(a1 + i * st, __float_as_int(v.y) - 0x4B400000);
+    }
+}
+
 // Deposit the three current components on a window of M nodes per axis
 // (M-1 half nodes along the current's own axis); node 0 of axis d sits at
-// tile index b[d].  cx..cz carry jcoef_d w times the chunk scale.
-template <int M, int PX, int TY, int NJ>
+// tile index b[d].  cx..cz carry jcoef_d w times the chunk scale.  With
+// PAIR (PCS: 144 atomics per move) the transverse factors and the
+// fixed-point conversions go two lines at a time through the packed FP32
+// pipe; for CIC and TSC the pairs' extra registers cost more than they save.
+template <int M, int PX, int TY, int NJ, bool PAIR>
 __device__ __forceinline__ void deposit_window(int* sJi, const int b[3], const float* S0x,
                                                const float* S0y, const float* S0z, const float* DSx,
                                                const float* DSy, const float* DSz, float cx, float cy,
@@ -345,12 +400,23 @@ __device__ __forceinline__ void deposit_window(int* sJi, const int b[3], const f
 #pragma unroll
         for (int k = 0; k < M; ++k)
 #pragma unroll
-            for (int j = 0; j < M; ++j) {
-                const float T = cx * esk_T(S0y[j], DSy[j], S0z[k], DSz[k]);
+            for (int j = 0; j < M; j += 2) {
                 int* row = sJi + (b[2] + k) * PY + (b[1] + j) * PX + b[0];
+                if (PAIR && j + 1 < M) {
+                    const float2 T = __fmul2_rn(dup2(cx), esk_T2(make_float2(S0y[j], S0y[j + 1]),
+                                                                make_float2(DSy[j], DSy[j + 1]),
+                                                                dup2(S0z[k]), dup2(DSz[k])));
+                    add_line_pair<M>(row, row + PX, 1, P, T);
+                } else {
 #pragma unroll
-                for (int i = 0; i < M - 1; ++i)
-                    atomicAdd(row + i, magic_int(P[i] * T));
+                    for (int jj = j; jj < (PAIR ? j + 1 : min(j + 2, M)); ++jj) {
+                        const float T = cx * esk_T(S0y[jj], DSy[jj], S0z[k], DSz[k]);
+                        int* r = row + (jj - j) * PX;
+#pragma unroll
+                        for (int i = 0; i < M - 1; ++i)
+                            atomicAdd(r + i, magic_int(P[i] * T));
+                    }
+                }
             }
     }
     {
@@ -362,12 +428,23 @@ __device__ __forceinline__ void deposit_window(int* sJi, const int b[3], const f
 #pragma unroll
         for (int k = 0; k < M; ++k)
 #pragma unroll
-            for (int i = 0; i < M; ++i) {
-                const float T = cy * esk_T(S0z[k], DSz[k], S0x[i], DSx[i]);
+            for (int i = 0; i < M; i += 2) {
                 int* col = sJi + NJ + (b[2] + k) * PY + b[1] * PX + (b[0] + i);
+                if (PAIR && i + 1 < M) {
+                    const float2 T = __fmul2_rn(dup2(cy), esk_T2(dup2(S0z[k]), dup2(DSz[k]),
+                                                                make_float2(S0x[i], S0x[i + 1]),
+                                                                make_float2(DSx[i], DSx[i + 1])));
+                    add_line_pair<M>(col, col + 1, PX, P, T);
+                } else {
 #pragma unroll
-                for (int j = 0; j < M - 1; ++j)
-                    atomicAdd(col + j * PX, magic_int(P[j] * T));
+                    for (int ii = i; ii < (PAIR ? i + 1 : min(i + 2, M)); ++ii) {
+                        const float T = cy * esk_T(S0z[k], DSz[k], S0x[ii], DSx[ii]);
+                        int* c = col + (ii - i);
+#pragma unroll
+                        for (int j = 0; j < M - 1; ++j)
+                            atomicAdd(c + j * PX, magic_int(P[j] * T));
+                    }
+                }
             }
     }
     {
@@ -379,12 +456,23 @@ __device__ __forceinline__ void deposit_window(int* sJi, const int b[3], const f
 #pragma unroll
         for (int j = 0; j < M; ++j)
 #pragma unroll
-            for (int i = 0; i < M; ++i) {
-                const float T = cz * esk_T(S0x[i], DSx[i], S0y[j], DSy[j]);
+            for (int i = 0; i < M; i += 2) {
                 int* col = sJi + 2 * NJ + b[2] * PY + (b[1] + j) * PX + (b[0] + i);
+                if (PAIR && i + 1 < M) {
+                    const float2 T = __fmul2_rn(dup2(cz), esk_T2(make_float2(S0x[i], S0x[i + 1]),
+                                                                make_float2(DSx[i], DSx[i + 1]),
+                                                                dup2(S0y[j]), dup2(DSy[j])));
+                    add_line_pair<M>(col, col + 1, PY, P, T);
+                } else {
 #pragma unroll
-                for (int k = 0; k < M - 1; ++k)
-                    atomicAdd(col + k * PY, magic_int(P[k] * T));
+                    for (int ii = i; ii < (PAIR ? i + 1 : min(i + 2, M)); ++ii) {
+                        const float T = cz * esk_T(S0x[ii], DSx[ii], S0y[j], DSy[j]);
+                        int* c = col + (ii - i);
+#pragma unroll
+                        for (int k = 0; k < M - 1; ++k)
+                            atomicAdd(c + k * PY, magic_int(P[k] * T));
+                    }
+                }
             }
     }
 }
@@ -453,6 +541,7 @@ struct Stage {
     int pid[C];   // particle ids (only when tracked)
     int kr[C];    // key << 16 | rank within key
     int perm[C];  // sorted position -> chunk position
+    int brk[C];   // PCS, by push position: bank << 16 | rank within the bank
 };
 
 // Deposit inputs of the chunk's moves, by sorted position s stored at slot
@@ -460,6 +549,23 @@ struct Stage {
 // kDepStride between lanes, and the skew puts the 32 lanes on 32 different
 // banks.
 __host__ __device__ constexpr int rslot(int s) { return s + (s >> 5); }
+
+// PCS (144 atomics per common-window move): the chunk's moves are
+// counting-sorted by the shared-memory bank of their window origin (every
+// atomic of a common-window deposit lands there plus an offset shared by all
+// lanes) and dealt over the deposit lanes: slot q takes bank-major position
+// deal_pos(q), so the 32 lanes of a deposit group take every (C/32)-th
+// position -- mostly 32 different banks.
+template <int C>
+__host__ __device__ constexpr int deal_slot(int p)
+{
+    return (p % (C / 32)) * 32 + p / (C / 32);
+}
+template <int C>
+__host__ __device__ constexpr int deal_pos(int q)
+{
+    return (q & 31) * (C / 32) + (q >> 5);
+}
 
 template <int C>
 struct Records {
@@ -494,7 +600,39 @@ struct SharedState {
     int item, any, nholes, nhead, nsrc;
     int ngen[2];             // general-window moves of the chunk
     unsigned bound_bits[2];  // float bits of the chunk's largest |jcoef w D|
+    int bh[32];              // PCS: moves of the chunk per bank of their window origin
 };
+
+// Bank of the common-window origin of a PCS particle in local cell `cell`
+// (up to an offset shared by all particles).
+template <class T>
+__device__ __forceinline__ int dep_bank(int cell)
+{
+    const int lx = cell % T::LX, ly = (cell / T::LX) % T::LY, lz = cell / (T::LX * T::LY);
+    return ((lz * T::TY + ly) * T::PX + lx) & 31;
+}
+
+// Exclusive prefix of the per-bank counts, bank `lane` in lane `lane`.
+__device__ __forceinline__ int bank_offsets(const int* bh, int lane)
+{
+    const int c = bh[lane];
+    int incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o)
+            incl += t;
+    }
+    return incl - c;
+}
+
+// Record slot of the move at push position sidx (all 32 lanes call it).
+template <int C>
+__device__ __forceinline__ int dealt_slot(const int* brk, int sidx, int cn, int boff)
+{
+    const int br = sidx < cn ? brk[sidx] : 0;
+    return deal_slot<C>(__shfl_sync(0xffffffffu, boff, br >> 16) + (br & 0xffff));
+}
 
 // Stored-order passes: start copying the particles of list slots
 // [base, base + cn) into the chunk stage (cell, offsets, momenta, weight;
@@ -576,7 +714,7 @@ __device__ __forceinline__ void deposit_common(int* sJi, const Records<C>& r, in
         }
     }
     const float ws = r.w[e] * scale;
-    deposit_window<NW, T::PX, T::TY, T::N>(sJi, b, S0[0], S0[1], S0[2], DS[0], DS[1], DS[2], jc[0] * ws,
+    deposit_window<NW, T::PX, T::TY, T::N, SHAPE == 3>(sJi, b, S0[0], S0[1], S0[2], DS[0], DS[1], DS[2], jc[0] * ws,
                                            jc[1] * ws, jc[2] * ws);
 }
 
@@ -622,7 +760,7 @@ __device__ __forceinline__ void deposit_general(int* sJi, const Records<C>& r, i
         }
     }
     const float ws = r.w[e] * scale;
-    deposit_window<M, T::PX, T::TY, T::N>(sJi, b, S0[0], S0[1], S0[2], DS[0], DS[1], DS[2], jc[0] * ws,
+    deposit_window<M, T::PX, T::TY, T::N, SHAPE == 3>(sJi, b, S0[0], S0[1], S0[2], DS[0], DS[1], DS[2], jc[0] * ws,
                                           jc[1] * ws, jc[2] * ws);
 }
 
@@ -719,7 +857,7 @@ __device__ __forceinline__ void store_part(const StepDev& d, int64_t idx, const 
 }
 
 // Pushes one particle (gather, Boris, move) and writes its deposit record
-// at position sidx of the chunk; returns its bound |jcoef_d w D_d| on the
+// at slot `slot` of the chunk; returns its bound |jcoef_d w D_d| on the
 // current terms.  A particle that stays in the supercell gets its new cell,
 // offsets and momentum in q; a leaver goes to the move buffer (its id read
 // from pidp when ids are tracked), q.cell becomes -1 and its list slot p
@@ -728,7 +866,7 @@ template <class T, int SHAPE, int NT>
 __device__ __forceinline__ float push_one(const StepDev& d, const SpeciesDev& sp, int s, const BoxDev& bx,
                                          int scx, int scy, int scz, const float* sF,
                                          SharedState<T, NT>& sh, Part& q, const int* pidp, int p,
-                                         int sidx, int cb, unsigned& my_status)
+                                         int slot, int cb, unsigned& my_status)
 {
     constexpr int LX = T::LX, LY = T::LY, LZ = T::LZ, N = T::N, PX = T::PX, TY = T::TY;
     constexpr int NW = SHAPE == 2 ? 3 : (SHAPE == 3 ? 4 : 2);
@@ -745,12 +883,25 @@ __device__ __forceinline__ float push_one(const StepDev& d, const SpeciesDev& sp
     // gather (Sec. 4: product of 1D weights at each Yee position)
     const bool ec = sp.ec != 0;
     AxisW<SHAPE> ax(lx + GO, ox, ec), ay(ly + GO, oy, ec), az(lz + GO, oz, ec);
-    const float Ex = gather_comp<NW, PX, TY>(sF + 0 * N, ax.bh, ay.bi, az.bi, ax.wh, ay.wi, az.wi);
-    const float Ey = gather_comp<NW, PX, TY>(sF + 1 * N, ax.bi, ay.bh, az.bi, ax.wi, ay.wh, az.wi);
-    const float Ez = gather_comp<NW, PX, TY>(sF + 2 * N, ax.bi, ay.bi, az.bh, ax.wi, ay.wi, az.wh);
-    const float Bx = gather_comp<NW, PX, TY>(sF + 3 * N, ax.bi, ay.bh, az.bh, ax.wi, ay.wh, az.wh);
-    const float By = gather_comp<NW, PX, TY>(sF + 4 * N, ax.bh, ay.bi, az.bh, ax.wh, ay.wi, az.wh);
-    const float Bz = gather_comp<NW, PX, TY>(sF + 5 * N, ax.bh, ay.bh, az.bi, ax.wh, ay.wh, az.wi);
+    // TSC and PCS: two components per packed FP32 instruction; CIC (8 terms
+    // a component) keeps the scalar form, which measured faster there
+    float Ex, Ey, Ez, Bx, By, Bz;
+    if (SHAPE != 1) {
+        const float2 Exy = gather_pair<NW, PX, TY>(sF + 0 * N, ax.bh, ay.bi, az.bi, ax.wh, ay.wi, az.wi,
+                                                   sF + 1 * N, ax.bi, ay.bh, az.bi, ax.wi, ay.wh, az.wi);
+        const float2 EzBx = gather_pair<NW, PX, TY>(sF + 2 * N, ax.bi, ay.bi, az.bh, ax.wi, ay.wi, az.wh,
+                                                    sF + 3 * N, ax.bi, ay.bh, az.bh, ax.wi, ay.wh, az.wh);
+        const float2 Byz = gather_pair<NW, PX, TY>(sF + 4 * N, ax.bh, ay.bi, az.bh, ax.wh, ay.wi, az.wh,
+                                                   sF + 5 * N, ax.bh, ay.bh, az.bi, ax.wh, ay.wh, az.wi);
+        Ex = Exy.x, Ey = Exy.y, Ez = EzBx.x, Bx = EzBx.y, By = Byz.x, Bz = Byz.y;
+    } else {
+        Ex = gather_comp<NW, PX, TY>(sF + 0 * N, ax.bh, ay.bi, az.bi, ax.wh, ay.wi, az.wi);
+        Ey = gather_comp<NW, PX, TY>(sF + 1 * N, ax.bi, ay.bh, az.bi, ax.wi, ay.wh, az.wi);
+        Ez = gather_comp<NW, PX, TY>(sF + 2 * N, ax.bi, ay.bi, az.bh, ax.wi, ay.wi, az.wh);
+        Bx = gather_comp<NW, PX, TY>(sF + 3 * N, ax.bi, ay.bh, az.bh, ax.wi, ay.wh, az.wh);
+        By = gather_comp<NW, PX, TY>(sF + 4 * N, ax.bh, ay.bi, az.bh, ax.wh, ay.wi, az.wh);
+        Bz = gather_comp<NW, PX, TY>(sF + 5 * N, ax.bh, ay.bh, az.bi, ax.wh, ay.wh, az.wi);
+    }
 
     // relativistic Boris push (Boris 1970): half kick, rotation, half kick
     const float eps = sp.eps;
@@ -781,7 +932,7 @@ __device__ __forceinline__ float push_one(const StepDev& d, const SpeciesDev& sp
                  ((oz >= 0.5f) == (z1 >= 0.5f));
     else
         common = x1 >= 0.0f && x1 < 1.0f && y1 >= 0.0f && y1 < 1.0f && z1 >= 0.0f && z1 < 1.0f;
-    const int rs = rslot(sidx);
+    const int rs = rslot(slot);
     rec.l[rs] = (lx + GO) | ((ly + GO) << 8) | ((lz + GO) << 16) | (common ? 0 : (1 << 24));
     rec.o[0][rs] = ox;
     rec.o[1][rs] = oy;
@@ -791,7 +942,7 @@ __device__ __forceinline__ float push_one(const StepDev& d, const SpeciesDev& sp
     rec.D[2][rs] = Dz;
     rec.w[rs] = w;
     if (!common)
-        rec.gen[atomicAdd(&sh.ngen[cb], 1)] = sidx;
+        rec.gen[atomicAdd(&sh.ngen[cb], 1)] = slot;
     // bound on every current term of this particle: |jcoef_d w P| with |P| <= |D_d|
     // (P is a difference of cumulative shape sums, whose slope is at most 1),
     // times |T| <= (max S)^2: 9/16 for TSC (S <= 3/4), 4/9 for PCS (S <= 2/3), 1 for CIC
@@ -880,6 +1031,7 @@ __device__ __forceinline__ void push_list(const StepDev& d, const SpeciesDev& sp
     constexpr int LX = T::LX, LY = T::LY, S = T::S, N = T::N;
     constexpr int C = SharedState<T, NT>::C;
     constexpr int K = Keys<T, SHAPE>::K;
+    constexpr bool DEAL = SHAPE == 3;  // bank-dealt deposit slots (see deal_slot)
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int L = s * d.nsc + g;
     const int n = d.count[L];
@@ -932,12 +1084,19 @@ __device__ __forceinline__ void push_list(const StepDev& d, const SpeciesDev& sp
             __syncthreads();
             for (int j = tid; j < cn; j += NT) {
                 const int kr = sh.st.kr[j];
-                sh.st.perm[sh.off[kr >> 16] + (kr & 0xffff)] = j;
+                const int ps = sh.off[kr >> 16] + (kr & 0xffff);
+                sh.st.perm[ps] = j;
+                if (DEAL) {
+                    const int bk = dep_bank<T>(sh.st.cell[j]);
+                    sh.st.brk[ps] = (bk << 16) | atomicAdd(&sh.bh[bk], 1);
+                }
             }
             __syncthreads();
+            const int boff = DEAL ? bank_offsets(sh.bh, lane) : 0;
             // push in sorted order: neighbouring lanes read neighbouring field words
             for (int s0 = 0; s0 < cn; s0 += NT) {
                 const int sidx = s0 + tid;
+                const int slot = DEAL ? dealt_slot<C>(sh.st.brk, sidx, cn, boff) : sidx;
                 float bnd = 0.0f;
                 if (sidx < cn) {
                     const int j = sh.st.perm[sidx];
@@ -951,7 +1110,7 @@ __device__ __forceinline__ void push_list(const StepDev& d, const SpeciesDev& sp
                     q.u[2] = sh.st.u[2][j];
                     q.w = sh.st.w[j];
                     bnd = push_one<T, SHAPE, NT>(d, sp, s, bx, scx, scy, scz, sF, sh, q, sh.st.pid + j,
-                                                 base + sidx, sidx, cb, my_status);
+                                                 base + sidx, slot, cb, my_status);
                     const int64_t idx = gidx(base + sidx);
                     store_part(d, idx, q, true);
                     if (d.pid && q.cell >= 0)
@@ -966,8 +1125,18 @@ __device__ __forceinline__ void push_list(const StepDev& d, const SpeciesDev& sp
             // particles displaced since): from the stage, which an async copy
             // filled while the previous chunk deposited, and back to the same
             // slot of the pool
+            int boff = 0;
+            if (DEAL) {
+                for (int j = tid; j < cn; j += NT) {
+                    const int bk = dep_bank<T>(sh.st.cell[j]);
+                    sh.st.brk[j] = (bk << 16) | atomicAdd(&sh.bh[bk], 1);
+                }
+                __syncthreads();
+                boff = bank_offsets(sh.bh, lane);
+            }
             for (int s0 = 0; s0 < cn; s0 += NT) {
                 const int sidx = s0 + tid;
+                const int slot = DEAL ? dealt_slot<C>(sh.st.brk, sidx, cn, boff) : sidx;
                 float bnd = 0.0f;
                 if (sidx < cn) {
                     const int64_t idx = gidx(base + sidx);
@@ -981,7 +1150,7 @@ __device__ __forceinline__ void push_list(const StepDev& d, const SpeciesDev& sp
                     q.u[2] = sh.st.u[2][sidx];
                     q.w = sh.st.w[sidx];
                     bnd = push_one<T, SHAPE, NT>(d, sp, s, bx, scx, scy, scz, sF, sh, q,
-                                                 d.pid ? d.pid + idx : nullptr, base + sidx, sidx, cb,
+                                                 d.pid ? d.pid + idx : nullptr, base + sidx, slot, cb,
                                                  my_status);
                     store_part(d, idx, q, false);
                 }
@@ -995,6 +1164,8 @@ __device__ __forceinline__ void push_list(const StepDev& d, const SpeciesDev& sp
             sh.ngen[cb ^ 1] = 0;
             sh.bound_bits[cb ^ 1] = 0u;
         }
+        if (DEAL && tid < 32)
+            sh.bh[tid] = 0;  // every warp read it before the barrier above; next written after the chunk
         if (!sort_pass && base + C < n)  // the stage is free: the next chunk flies during the deposit
             stage_chunk_async<T, NT>(d, sh, L, base + C, min(C, n - base - C));
         // deposit: neighbouring lanes take chunk positions kDepStride apart
@@ -1004,8 +1175,8 @@ __device__ __forceinline__ void push_list(const StepDev& d, const SpeciesDev& sp
         const float scale = chunk_scale(cn, __uint_as_float(sh.bound_bits[cb]), &inv);
         for (int r = 0; r < C / NT; ++r) {
             const int q = r * NT + tid;
-            const int e = kDepStride * (q % (C / kDepStride)) + q / (C / kDepStride);
-            if (e < cn && !(sh.rec.l[rslot(e)] >> 24))
+            const int e = DEAL ? q : kDepStride * (q % (C / kDepStride)) + q / (C / kDepStride);
+            if ((DEAL ? deal_pos<C>(q) : e) < cn && !(sh.rec.l[rslot(e)] >> 24))
                 deposit_common<T, SHAPE, C>(sJi, sh.rec, e, sp.jcoef, scale);
         }
         // general-window moves: whole groups of 32 lane-parallel, one group
@@ -1131,6 +1302,8 @@ __global__ void __launch_bounds__(NT, (T::G == 1 ? 1024 : 512) / NT) k_push_depo
     // current one, and publishes it at the end of the item
     if (tid == 0)
         sh.item = atomicAdd(d.work_counter, 1);
+    if (tid < 32)
+        sh.bh[tid] = 0;  // each chunk clears it after use
     __syncthreads();
     for (;;) {
         const int item = sh.item;

@@ -30,7 +30,7 @@ def test_committed_profile_has_every_figure():
     assert len(vals["k_push.cu sha256"]) == 64
     assert 60.0 < float(vals["dram bytes per particle"]) < 80.0   # 64.5 B algorithmic
     assert 5.0 < float(vals["shared wavefronts per particle"]) < 40.0
-    assert 100.0 < float(vals["fp32 instructions per particle"]) < 3000.0
+    assert 100.0 < float(vals["fp32 operations per particle"]) < 3000.0
 
 
 def test_profile_is_used_only_for_the_kernel_it_was_taken_on(tmp_path, monkeypatch):
@@ -40,7 +40,7 @@ def test_profile_is_used_only_for_the_kernel_it_was_taken_on(tmp_path, monkeypat
     sha = hashlib.sha256(src.read_bytes()).hexdigest()
     md = tmp_path / "profile.md"
     md.write_text(f"- k_push.cu sha256: `{sha}`\n- dram bytes per particle: `64.5`\n"
-                  f"- shared wavefronts per particle: `17.0`\n- fp32 instructions per particle: `670`\n")
+                  f"- shared wavefronts per particle: `17.0`\n- fp32 operations per particle: `670`\n")
     monkeypatch.setattr(bench, "PUSH_KERNEL_SRC", str(src))
     monkeypatch.setattr(bench, "TRAFFIC_SUMMARY", str(md))
     assert bench.push_profile() == {"tpp": 64.5, "wpp": 17.0, "fpp": 670.0}
