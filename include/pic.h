@@ -207,7 +207,10 @@ pic_status pic_shift_window(pic_ctx* ctx, int32_t box, int32_t cells);
  *   w[n]    weights, or NULL for all ones.
  * All host arrays are read, not kept.  With track_ids the particles get ids
  * equal to their running load index within (box, species).  Returns
- * PIC_ERR_ARG for non-finite input.
+ * PIC_ERR_ARG for non-finite input.  Mixed form: when every array lies in one
+ * page-locked host allocation (cudaHostAlloc, cudaHostRegister), the
+ * conversion kernel reads it in place over the host link; otherwise the
+ * arrays are staged through device memory.  The results are the same.
  */
 pic_status pic_load_particles(pic_ctx* ctx, int32_t box, int32_t species, int64_t n,
                               const double* x, const double* u, const double* w);
@@ -254,6 +257,9 @@ pic_status pic_count_particles(pic_ctx* ctx, int32_t box, int32_t species, int64
  * (optional, NULL to skip; requires track_ids).  Any of x, u, w may be NULL
  * to skip it.  The order is unspecified (frames reorder particles).  *n_out
  * receives the count; PIC_ERR_ARG if it exceeds cap (nothing is copied).
+ * Mixed form: when every requested array lies in one page-locked host
+ * allocation, the conversion kernel writes it in place; otherwise through
+ * a device staging buffer.
  */
 pic_status pic_read_particles(pic_ctx* ctx, int32_t box, int32_t species, int64_t cap,
                               double* x, double* u, double* w, int64_t* id, int64_t* n_out);
@@ -287,7 +293,9 @@ pic_status pic_stage_times(pic_ctx* ctx, double ms[4], int64_t* nsteps_out);
  *   PIC_INFO_POOL_FRAMES     frame-pool capacity (mixed form);
  *   PIC_INFO_FRAMES_USED     frames holding particles, read from the device;
  *   PIC_INFO_MOVE_CAPACITY   capacity of the per-step buffer of particles changing supercell;
- *   PIC_INFO_STEPS           steps taken since pic_create (the time of E is STEPS * dt).
+ *   PIC_INFO_STEPS           steps taken since pic_create (the time of E is STEPS * dt);
+ *   PIC_INFO_HOST_DIRECT     pic_load_particles / pic_read_particles calls of the mixed form
+ *                            that converted page-locked host arrays in place.
  */
 enum {
     PIC_INFO_GRAPH_ACTIVE = 0,
@@ -295,7 +303,8 @@ enum {
     PIC_INFO_POOL_FRAMES = 2,
     PIC_INFO_FRAMES_USED = 3,
     PIC_INFO_MOVE_CAPACITY = 4,
-    PIC_INFO_STEPS = 5
+    PIC_INFO_STEPS = 5,
+    PIC_INFO_HOST_DIRECT = 6
 };
 pic_status pic_info(pic_ctx* ctx, int32_t key, int64_t* out);
 

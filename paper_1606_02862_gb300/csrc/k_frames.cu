@@ -345,7 +345,10 @@ cudaError_t launch_insert_convert(const StepDev& d, int box, int species, int64_
 }
 
 // One CTA per supercell of the box: copy its particles to FP64 global form
-// at list_off[sc] (exclusive prefix of the counts, host-computed).
+// at list_off[sc] (exclusive prefix of the counts, host-computed).  Thread j
+// writes word j of the supercell's run of x (and of u), so that every warp
+// store covers 256 contiguous bytes: the destination may be page-locked host
+// memory written over the host link, where partial sectors cost.
 __global__ void k_read_particles(const StepDev d, int box, int species, const int* list_off,
                                  double* x, double* u, double* w, int64_t* id)
 {
@@ -357,26 +360,26 @@ __global__ void k_read_particles(const StepDev d, int box, int species, const in
     const int scx = loc % b.nscx, scy = (loc / b.nscx) % b.nscy, scz = loc / (b.nscx * b.nscy);
     const int* ft = d.ftab + d.foff[L];
     const int64_t o0 = list_off[loc];
-    for (int p = threadIdx.x; p < n; p += blockDim.x) {
+    for (int j = threadIdx.x; j < 3 * n; j += blockDim.x) {
+        const int p = j / 3, a = j - 3 * p;
         const int64_t idx = (int64_t)ft[p >> d.log2S] * d.S + (p & (d.S - 1));
-        const int cell = d.cell[idx];
-        const int lx = cell % d.LX, ly = (cell / d.LX) % d.LY, lz = cell / (d.LX * d.LY);
-        const int64_t o = o0 + p;
         if (x) {
-            x[3 * o + 0] = (double)(scx * d.LX + lx) + (double)d.ox[idx];
-            x[3 * o + 1] = (double)(scy * d.LY + ly) + (double)d.oy[idx];
-            x[3 * o + 2] = (double)(scz * d.LZ + lz) + (double)d.oz[idx];
+            const int cell = d.cell[idx];
+            const int gc = a == 0 ? scx * d.LX + cell % d.LX
+                                  : (a == 1 ? scy * d.LY + (cell / d.LX) % d.LY : scz * d.LZ + cell / (d.LX * d.LY));
+            x[3 * o0 + j] = (double)gc + (double)(a == 0 ? d.ox : (a == 1 ? d.oy : d.oz))[idx];
         }
-        if (u) {
-            u[3 * o + 0] = (double)d.ux[idx];
-            u[3 * o + 1] = (double)d.uy[idx];
-            u[3 * o + 2] = (double)d.uz[idx];
-        }
-        if (w)
-            w[o] = (double)d.w[idx];
-        if (id)
-            id[o] = d.pid ? (int64_t)d.pid[idx] : -1;
+        if (u)
+            u[3 * o0 + j] = (double)(a == 0 ? d.ux : (a == 1 ? d.uy : d.uz))[idx];
     }
+    if (w || id)
+        for (int p = threadIdx.x; p < n; p += blockDim.x) {
+            const int64_t idx = (int64_t)ft[p >> d.log2S] * d.S + (p & (d.S - 1));
+            if (w)
+                w[o0 + p] = (double)d.w[idx];
+            if (id)
+                id[o0 + p] = d.pid ? (int64_t)d.pid[idx] : -1;
+        }
 }
 
 cudaError_t launch_read_particles(const StepDev& d, const BoxDev& hb, int box, int species,

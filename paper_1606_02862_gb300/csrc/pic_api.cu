@@ -8,6 +8,8 @@
 #include "pic_internal.cuh"
 #include "plain.cuh"
 
+#include <cuda.h>  // pointer-attribute types only; the driver call goes through cudaGetDriverEntryPointByVersion
+
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
@@ -96,6 +98,7 @@ struct pic_ctx {
     int* step_ctr = nullptr;           // device step count, read by the push for its sort passes
     long long* step_no = nullptr;      // device: steps taken since creation (antenna time)
     int64_t steps_done = 0;            // host: steps enqueued since creation
+    int64_t host_direct = 0;           // load / read calls that converted page-locked host arrays in place
     int* abs_off_d = nullptr;          // [nboxes + 1] block offsets of the y absorber
     int abs_nblocks = 0;
     bool any_antenna = false;
@@ -241,6 +244,51 @@ pic_status ensure_stage(pic_ctx* c, size_t bytes)
     c->stage_d = p;
     c->stage_bytes = bytes;
     return PIC_OK;
+}
+
+// Device address of the host range [p, p + bytes) when all of it lies in one
+// page-locked host allocation mapped into this device's address space
+// (cudaHostAlloc / cudaHostRegister, e.g. torch pin_memory); nullptr
+// otherwise, and then the caller stages through device memory.  The particle
+// conversion kernels read and write such buffers directly over the host
+// link, which saves the staging buffer and a copy.  The allocation's extent
+// comes from the driver (cuPointerGetAttribute, reached through the runtime's
+// entry-point query, so libpic needs no link to the driver library); when
+// that query is unavailable the range is not used directly.
+const void* host_range_on_device(const void* p, size_t bytes)
+{
+    if (!p || bytes == 0)
+        return nullptr;
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type != cudaMemoryTypeHost || !a.devicePointer)
+        return nullptr;
+    using GetAttr = CUresult (*)(void*, CUpointer_attribute, CUdeviceptr);
+    static GetAttr get_attr = [] {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuPointerGetAttribute", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            fn = nullptr;
+        }
+        return reinterpret_cast<GetAttr>(fn);
+    }();
+    if (!get_attr)
+        return nullptr;
+    const CUdeviceptr dp = reinterpret_cast<CUdeviceptr>(a.devicePointer);
+    CUdeviceptr start = 0;
+    size_t size = 0;
+    if (get_attr(&start, CU_POINTER_ATTRIBUTE_RANGE_START_ADDR, dp) != CUDA_SUCCESS ||
+        get_attr(&size, CU_POINTER_ATTRIBUTE_RANGE_SIZE, dp) != CUDA_SUCCESS)
+        return nullptr;
+    if (dp < start || dp - start > size || bytes > size - (dp - start))
+        return nullptr;
+    return a.devicePointer;
 }
 
 pic_status ensure_ioff(pic_ctx* c, int64_t n)
@@ -1063,21 +1111,64 @@ pic_status pic_load_particles(pic_ctx* c, int32_t box, int32_t species, int64_t 
     // captured step graphs stay valid unless a buffer they use is reallocated
     // (ensure_pool / ensure_mv drop them) or a weight bound grows (below)
     const int64_t chunk = std::min<int64_t>(n, 1 << 25);  // 32 M particles: 1.9 GB of FP64 staging
-    CKS(ensure_stage(c, sizeof(double) * 7 * (size_t)chunk));
-    double* sx = static_cast<double*>(c->stage_d);
-    double* su = sx + 3 * chunk;
-    double* sw = su + 3 * chunk;
+    // mixed form from page-locked host arrays: the conversion reads them in place
+    const double* hx = nullptr;
+    const double* hu = nullptr;
+    const double* hw = nullptr;
+    if (c->precision != PIC_PRECISION_FP64_PLAIN) {
+        hx = static_cast<const double*>(host_range_on_device(x, sizeof(double) * 3 * (size_t)n));
+        hu = static_cast<const double*>(host_range_on_device(u, sizeof(double) * 3 * (size_t)n));
+        hw = w ? static_cast<const double*>(host_range_on_device(w, sizeof(double) * (size_t)n)) : nullptr;
+    }
+    const bool direct = hx && hu && (!w || hw);
+    if (direct)
+        ++c->host_direct;
+    else
+        CKS(ensure_stage(c, sizeof(double) * 7 * (size_t)chunk));
+    if (c->precision != PIC_PRECISION_FP64_PLAIN) {
+        // one pool growth for the whole call instead of one per chunk (each
+        // growth reallocates and copies every pool array): room for what the
+        // call can add -- every particle, plus one part-filled frame per list
+        // of the box -- and for the first step's headroom (prepare_mixed), so
+        // that the first step does not grow the pool either.  A capacity set
+        // in the options is taken as given (the chunks below still add what
+        // an insertion needs beyond it).
+        if (c->opt.pool_frames > 0) {
+            CKS(ensure_pool(c, c->opt.pool_frames));
+        } else {
+            int top = 0;
+            if (c->pool_cap > 0)
+                CKS(read_free_top(c, &top));
+            const BoxDev& bd = c->boxes_h[box];
+            const int64_t lists = (int64_t)bd.nscx * bd.nscy * bd.nscz;
+            const int64_t after = (c->pool_cap - top) + (n + c->S - 1) / c->S + std::min<int64_t>(n, lists);
+            CKS(ensure_pool(c, after + after / 4 + c->nlists / 4 + 1024));
+        }
+    }
     for (int64_t b0 = 0; b0 < n; b0 += chunk) {
         const int64_t m = std::min(chunk, n - b0);
-        CK(cudaMemcpyAsync(sx, x + 3 * b0, sizeof(double) * 3 * m, cudaMemcpyHostToDevice, c->stream));
-        CK(cudaMemcpyAsync(su, u + 3 * b0, sizeof(double) * 3 * m, cudaMemcpyHostToDevice, c->stream));
-        if (w)
-            CK(cudaMemcpyAsync(sw, w + b0, sizeof(double) * m, cudaMemcpyHostToDevice, c->stream));
+        const double *sx, *su, *sw;
+        if (direct) {
+            sx = hx + 3 * b0;
+            su = hu + 3 * b0;
+            sw = w ? hw + b0 : nullptr;
+        } else {
+            double* st = static_cast<double*>(c->stage_d);
+            CK(cudaMemcpyAsync(st, x + 3 * b0, sizeof(double) * 3 * m, cudaMemcpyHostToDevice, c->stream));
+            CK(cudaMemcpyAsync(st + 3 * chunk, u + 3 * b0, sizeof(double) * 3 * m, cudaMemcpyHostToDevice,
+                               c->stream));
+            if (w)
+                CK(cudaMemcpyAsync(st + 6 * chunk, w + b0, sizeof(double) * m, cudaMemcpyHostToDevice,
+                                   c->stream));
+            sx = st;
+            su = st + 3 * chunk;
+            sw = w ? st + 6 * chunk : nullptr;
+        }
         if (c->precision == PIC_PRECISION_FP64_PLAIN) {
             PlainSpecies& s = c->pboxes[box].sp[species];
             CKS(plain_grow(c, s, s.n + m));
             const pic_grid& g = c->grids[box];
-            CK(launch_plain_load(m, sx, su, w ? sw : nullptr, g.nx, g.ny, g.nz, s.x + s.n, s.y + s.n,
+            CK(launch_plain_load(m, sx, su, sw, g.nx, g.ny, g.nz, s.x + s.n, s.y + s.n,
                                  s.z + s.n, s.ux + s.n, s.uy + s.n, s.uz + s.n, s.w + s.n,
                                  s.pid ? s.pid + s.n : nullptr, (int)(idn + b0), c->status_d,
                                  c->stream));
@@ -1093,7 +1184,7 @@ pic_status pic_load_particles(pic_ctx* c, int32_t box, int32_t species, int64_t 
         } else {
             CKS(ensure_mv(c, std::max<int64_t>(c->mv_cap, m)));
             StepDev d = make_step(c, c->parity);
-            CK(launch_insert_convert(d, box, species, m, sx, su, w ? sw : nullptr, (int)(idn + b0),
+            CK(launch_insert_convert(d, box, species, m, sx, su, sw, (int)(idn + b0),
                                      c->stream));
             int mi = (int)m;
             CK(cudaMemcpyAsync(c->mv_count, &mi, sizeof(int), cudaMemcpyHostToDevice, c->stream));
@@ -1225,6 +1316,44 @@ pic_status pic_count_particles(pic_ctx* c, int32_t box, int32_t species, int64_t
     return PIC_OK;
 }
 
+namespace {
+
+// Mixed form: convert the (box, species) particles to FP64 into the device
+// addresses dx, du, dw, di (each may be null); when a host destination hx..hi
+// is given, copy the converted array there afterwards.
+pic_status read_particles_mixed(pic_ctx* c, int box, int species, double* dx, double* du, double* dw,
+                                int64_t* di, double* hx, double* hu, double* hw, int64_t* hi)
+{
+    const BoxDev& b = c->boxes_h[box];
+    const int nscb = b.nscx * b.nscy * b.nscz;
+    std::vector<int> cnt(nscb), off(nscb);
+    CK(cudaMemcpyAsync(cnt.data(), c->count + (size_t)species * c->nsc + b.sc_base, sizeof(int) * nscb,
+                       cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    int64_t acc = 0;
+    for (int i = 0; i < nscb; ++i) {
+        off[i] = (int)acc;
+        acc += cnt[i];
+    }
+    const int64_t n = acc;
+    CKS(ensure_ioff(c, nscb));
+    CK(cudaMemcpyAsync(c->ioff_d, off.data(), sizeof(int) * nscb, cudaMemcpyHostToDevice, c->stream));
+    StepDev d = make_step(c, c->parity);
+    CK(launch_read_particles(d, b, box, species, c->ioff_d, dx, du, dw, di, c->stream));
+    if (hx)
+        CK(cudaMemcpyAsync(hx, dx, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, c->stream));
+    if (hu)
+        CK(cudaMemcpyAsync(hu, du, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, c->stream));
+    if (hw)
+        CK(cudaMemcpyAsync(hw, dw, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
+    if (hi)
+        CK(cudaMemcpyAsync(hi, di, sizeof(int64_t) * n, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return PIC_OK;
+}
+
+}  // namespace
+
 pic_status pic_read_particles(pic_ctx* c, int32_t box, int32_t species, int64_t cap, double* x,
                               double* u, double* w, int64_t* id, int64_t* n_out)
 {
@@ -1242,6 +1371,19 @@ pic_status pic_read_particles(pic_ctx* c, int32_t box, int32_t species, int64_t 
                     (long long)n);
     if (n == 0)
         return PIC_OK;
+    // mixed form into page-locked host arrays: the conversion writes them in place
+    if (c->precision != PIC_PRECISION_FP64_PLAIN) {
+        void* dx = x ? const_cast<void*>(host_range_on_device(x, sizeof(double) * 3 * (size_t)n)) : nullptr;
+        void* du = u ? const_cast<void*>(host_range_on_device(u, sizeof(double) * 3 * (size_t)n)) : nullptr;
+        void* dw = w ? const_cast<void*>(host_range_on_device(w, sizeof(double) * (size_t)n)) : nullptr;
+        void* di = id ? const_cast<void*>(host_range_on_device(id, sizeof(int64_t) * (size_t)n)) : nullptr;
+        if ((!x || dx) && (!u || du) && (!w || dw) && (!id || di)) {
+            ++c->host_direct;
+            return read_particles_mixed(c, box, species, static_cast<double*>(dx), static_cast<double*>(du),
+                                        static_cast<double*>(dw), static_cast<int64_t*>(di), nullptr, nullptr,
+                                        nullptr, nullptr);
+        }
+    }
     CKS(ensure_stage(c, sizeof(double) * 7 * (size_t)n + sizeof(int64_t) * (size_t)n));
     double* sx = static_cast<double*>(c->stage_d);
     double* su = sx + 3 * n;
@@ -1267,31 +1409,7 @@ pic_status pic_read_particles(pic_ctx* c, int32_t box, int32_t species, int64_t 
         CK(cudaStreamSynchronize(c->stream));
         return PIC_OK;
     }
-    const BoxDev& b = c->boxes_h[box];
-    const int nscb = b.nscx * b.nscy * b.nscz;
-    std::vector<int> cnt(nscb), off(nscb);
-    CK(cudaMemcpyAsync(cnt.data(), c->count + (size_t)species * c->nsc + b.sc_base, sizeof(int) * nscb,
-                       cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
-    int64_t acc = 0;
-    for (int i = 0; i < nscb; ++i) {
-        off[i] = (int)acc;
-        acc += cnt[i];
-    }
-    CKS(ensure_ioff(c, nscb));
-    CK(cudaMemcpyAsync(c->ioff_d, off.data(), sizeof(int) * nscb, cudaMemcpyHostToDevice, c->stream));
-    StepDev d = make_step(c, c->parity);
-    CK(launch_read_particles(d, b, box, species, c->ioff_d, sx, su, sw, id ? sid : nullptr, c->stream));
-    if (x)
-        CK(cudaMemcpyAsync(x, sx, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, c->stream));
-    if (u)
-        CK(cudaMemcpyAsync(u, su, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, c->stream));
-    if (w)
-        CK(cudaMemcpyAsync(w, sw, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
-    if (id)
-        CK(cudaMemcpyAsync(id, sid, sizeof(int64_t) * n, cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
-    return PIC_OK;
+    return read_particles_mixed(c, box, species, sx, su, sw, id ? sid : nullptr, x, u, w, id);
 }
 
 pic_status pic_diagnostics(pic_ctx* c, int32_t box, double out[4])
@@ -1414,6 +1532,9 @@ pic_status pic_info(pic_ctx* c, int32_t key, int64_t* out)
     }
     case PIC_INFO_STEPS:
         *out = c->steps_done;
+        return PIC_OK;
+    case PIC_INFO_HOST_DIRECT:
+        *out = c->host_direct;
         return PIC_OK;
     case PIC_INFO_MOVE_CAPACITY:
         *out = c->mv_cap;

@@ -35,7 +35,7 @@ EXPORTED = ("pic_create", "pic_set_background", "pic_set_boundary", "pic_set_ant
             "pic_read_particles", "pic_diagnostics", "pic_stage_timing", "pic_stage_times",
             "pic_info", "pic_field_energy_noalloc", "pic_last_error", "pic_destroy")
 (INFO_GRAPH_ACTIVE, INFO_KERNELS_PER_STEP, INFO_POOL_FRAMES, INFO_FRAMES_USED, INFO_MOVE_CAPACITY,
- INFO_STEPS) = range(6)
+ INFO_STEPS, INFO_HOST_DIRECT) = range(7)
 
 
 class PicError(RuntimeError):
