@@ -162,3 +162,27 @@ def test_pinned_subrange_of_a_larger_buffer():
     finally:
         a.close()
         b.close()
+
+
+def test_pinned_load_without_weights():
+    """w = NULL (all ones) on the in-place path equals the staged path."""
+    from paper_1606_02862_gb300 import pic
+
+    torch = require_gpu()
+    n, x, u, _ = _state(seed=8)
+    npart = x.shape[0]
+    Xp, Up = _pinned(torch, x), _pinned(torch, u)
+    a = _ctx(n)
+    b = _ctx(n)
+    try:
+        a.load_particles(0, 0, x, u)
+        b.load_particles_ptr(0, 0, npart, Xp.data_ptr(), Up.data_ptr(), None)
+        assert b.info(pic.INFO_HOST_DIRECT) == 1
+        ra = _by_id(_read(torch, a, npart, pinned=False))
+        rb = _by_id(_read(torch, b, npart, pinned=True))
+        for va, vb in zip(ra, rb):
+            assert np.array_equal(va, vb)
+        assert np.all(rb[2] == 1.0)
+    finally:
+        a.close()
+        b.close()
