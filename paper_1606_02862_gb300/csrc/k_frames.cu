@@ -281,20 +281,41 @@ cudaError_t launch_frame_apply(const StepDev& d, int place_blocks, cudaStream_t 
 
 // ------------------------------------------------------------ load / read
 
-// Host particles (FP64, n x 3 global cell coordinates) -> move buffer.
-__global__ void k_insert_convert(const StepDev d, int box, int species, int n, const double* x,
-                                 const double* u, const double* w, int id_base)
+// Host particles (FP64, n x 3 global cell coordinates) -> move buffer.  A
+// block takes 256 particles at a time: their x, u and w runs come into
+// shared memory word by word across the threads (each warp load is 256
+// contiguous bytes: the source may be page-locked host memory read over the
+// host link), then each thread converts one particle.
+constexpr int kInsertBlock = 256;
+
+__global__ void __launch_bounds__(kInsertBlock) k_insert_convert(const StepDev d, int box, int species, int n,
+                                                                 const double* x, const double* u,
+                                                                 const double* w, int id_base)
 {
+    __shared__ double sx[3 * kInsertBlock], su[3 * kInsertBlock], sw[kInsertBlock];
     const BoxDev b = d.boxes[box];
     const int Nd[3] = {b.nx, b.ny, b.nz};
     const int Ld[3] = {d.LX, d.LY, d.LZ};
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    for (int64_t base = (int64_t)blockIdx.x * kInsertBlock; base < n; base += (int64_t)gridDim.x * kInsertBlock) {
+        const int m = (int)(n - base < kInsertBlock ? n - base : kInsertBlock);
+        __syncthreads();  // the previous group's reads of the stage are done
+        for (int j = threadIdx.x; j < 3 * m; j += kInsertBlock) {
+            sx[j] = x[3 * base + j];
+            su[j] = u[3 * base + j];
+        }
+        if (threadIdx.x < m)
+            sw[threadIdx.x] = w ? w[base + threadIdx.x] : 1.0;
+        __syncthreads();
+        if (threadIdx.x >= m)
+            continue;
+        const int t = threadIdx.x;
+        const int i = (int)(base + t);
         int scd[3], lc[3];
         float o[3];
         bool bad = false;
         for (int a = 0; a < 3; ++a) {
-            double v = x[3 * (int64_t)i + a];
-            if (!isfinite(v) || !isfinite(u[3 * (int64_t)i + a]))
+            double v = sx[3 * t + a];
+            if (!isfinite(v) || !isfinite(su[3 * t + a]))
                 bad = true;
             double N = (double)Nd[a];
             v = v - N * floor(v / N);
@@ -310,7 +331,7 @@ __global__ void k_insert_convert(const StepDev d, int box, int species, int n, c
             scd[a] = ci / Ld[a];
             lc[a] = ci - scd[a] * Ld[a];
         }
-        double wv = w ? w[i] : 1.0;
+        const double wv = sw[t];
         if (!isfinite(wv))
             bad = true;
         if (bad)
@@ -325,9 +346,9 @@ __global__ void k_insert_convert(const StepDev d, int box, int species, int n, c
         d.mv_ox[i] = o[0];
         d.mv_oy[i] = o[1];
         d.mv_oz[i] = o[2];
-        d.mv_ux[i] = (float)u[3 * (int64_t)i + 0];
-        d.mv_uy[i] = (float)u[3 * (int64_t)i + 1];
-        d.mv_uz[i] = (float)u[3 * (int64_t)i + 2];
+        d.mv_ux[i] = (float)su[3 * t + 0];
+        d.mv_uy[i] = (float)su[3 * t + 1];
+        d.mv_uz[i] = (float)su[3 * t + 2];
         d.mv_w[i] = (float)wv;
         if (d.mv_pid)
             d.mv_pid[i] = id_base + i;
@@ -338,9 +359,9 @@ cudaError_t launch_insert_convert(const StepDev& d, int box, int species, int64_
                                   const double* x, const double* u, const double* w, int id_base,
                                   cudaStream_t st)
 {
-    int blocks = (int)std::min<int64_t>((n + 255) / 256, 4096);
+    int blocks = (int)std::min<int64_t>((n + kInsertBlock - 1) / kInsertBlock, 4096);
     if (blocks > 0)
-        k_insert_convert<<<blocks, 256, 0, st>>>(d, box, species, (int)n, x, u, w, id_base);
+        k_insert_convert<<<blocks, kInsertBlock, 0, st>>>(d, box, species, (int)n, x, u, w, id_base);
     return cudaGetLastError();
 }
 
