@@ -398,7 +398,8 @@ def run_ours(args, rank, world, dist):
         Xo = torch.empty_like(X, pin_memory=True)
         Uo = torch.empty_like(U, pin_memory=True)
         Wo = torch.empty_like(Wt, pin_memory=True)
-        Eo = np.empty((3, n, n, n))
+        Eo_t = torch.empty((3, n, n, n), dtype=torch.float64, pin_memory=True)
+        Eo = Eo_t.numpy()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         ctx = new_ctx(pic, n, pic.PRECISION_MIXED, sc, args.threads, SHAPE[args.shape], GATHER[args.gather])

@@ -242,7 +242,8 @@ pic_status pic_sync(pic_ctx* ctx);
  * pic_read_fields -- copy field `which` of box `box` into out[3*nz*ny*nx]
  * (PIC_FIELD_E, _B, _J) or out[nz*ny*nx] (PIC_FIELD_RHO, the charge density
  * at the nodes including the background), host, FP64, x fastest.  J is the
- * current of the last step (J^{n+1/2}).
+ * current of the last step (J^{n+1/2}).  Mixed form, E/B/J: a page-locked
+ * destination is written in place by the conversion kernel.
  */
 pic_status pic_read_fields(pic_ctx* ctx, int32_t box, int32_t which, double* out);
 
@@ -294,8 +295,8 @@ pic_status pic_stage_times(pic_ctx* ctx, double ms[4], int64_t* nsteps_out);
  *   PIC_INFO_FRAMES_USED     frames holding particles, read from the device;
  *   PIC_INFO_MOVE_CAPACITY   capacity of the per-step buffer of particles changing supercell;
  *   PIC_INFO_STEPS           steps taken since pic_create (the time of E is STEPS * dt);
- *   PIC_INFO_HOST_DIRECT     pic_load_particles / pic_read_particles calls of the mixed form
- *                            that converted page-locked host arrays in place.
+ *   PIC_INFO_HOST_DIRECT     pic_load_particles / pic_read_particles / pic_read_fields calls
+ *                            of the mixed form that converted page-locked host arrays in place.
  */
 enum {
     PIC_INFO_GRAPH_ACTIVE = 0,

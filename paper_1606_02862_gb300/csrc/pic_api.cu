@@ -1460,6 +1460,10 @@ pic_status pic_read_fields(pic_ctx* c, int32_t box, int32_t which, double* out)
         const PlainBox& b = c->pboxes[box];
         const double* src = which == PIC_FIELD_E ? b.E : (which == PIC_FIELD_B ? b.B : b.J);
         CK(cudaMemcpyAsync(out, src, sizeof(double) * 3 * nc, cudaMemcpyDeviceToHost, c->stream));
+    } else if (void* dout = const_cast<void*>(host_range_on_device(out, sizeof(double) * 3 * nc))) {
+        // page-locked destination: the conversion writes it in place
+        ++c->host_direct;
+        CK(launch_fields_from_padded(c->boxes_h[box], which, static_cast<double*>(dout), c->stream));
     } else {
         CKS(ensure_stage(c, sizeof(double) * 3 * nc));
         CK(launch_fields_from_padded(c->boxes_h[box], which, static_cast<double*>(c->stage_d),

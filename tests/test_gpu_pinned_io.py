@@ -186,3 +186,26 @@ def test_pinned_load_without_weights():
     finally:
         a.close()
         b.close()
+
+
+def test_pinned_field_read():
+    """pic_read_fields into a page-locked array equals the staged read."""
+    from paper_1606_02862_gb300 import pic
+
+    torch = require_gpu()
+    n, x, u, w = _state(seed=9)
+    ctx = _ctx(n)
+    try:
+        ctx.load_particles(0, 0, x, u, w)
+        ctx.step(2)
+        nx, ny, nz = n
+        for which in (pic.FIELD_E, pic.FIELD_B, pic.FIELD_J):
+            before = ctx.info(pic.INFO_HOST_DIRECT)
+            ref = ctx.read_fields(0, which)
+            assert ctx.info(pic.INFO_HOST_DIRECT) == before
+            out = torch.empty((3, nz, ny, nx), dtype=torch.float64, pin_memory=True)
+            ctx.read_fields_ptr(0, which, out.data_ptr())
+            assert ctx.info(pic.INFO_HOST_DIRECT) == before + 1
+            assert np.array_equal(out.numpy(), ref)
+    finally:
+        ctx.close()
