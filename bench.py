@@ -738,6 +738,12 @@ def main():
     if world > 1:
         import torch.distributed as dist_mod
 
+        if args.impl == "ours":
+            import torch
+
+            # each rank's GPU before the NCCL group forms, so that its
+            # communicator binds to that device
+            torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         dist_mod.init_process_group("nccl" if args.impl == "ours" else "gloo")
         dist = dist_mod
     if args.impl == "reference":
