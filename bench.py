@@ -456,10 +456,7 @@ def run_ours(args, rank, world, dist):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": result["step_ms"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": f"thermal_{args.shape}_{n}: {n}^3 periodic cells, electrons {ppc} ppc "
-                               f"({npart} particles/GPU), u_th 0.05c, {args.shape.upper()}, "
-                               "dt = 0.5 Courant, neutralising background"
-                               + (", energy-conserving gather" if args.gather == "energy" else ""),
+        "config": {"workload": thermal_workload_name(args, n, ppc),
                    "form": f"mixed: int32 cell + FP32 offsets, supercell frames {args.sc}, "
                            f"{args.threads or 'default'} threads/supercell",
                    "graph": result["graph"],
@@ -676,6 +673,14 @@ def run_window(args):
 
 # ----------------------------------------------------------------------------- reference arm
 
+def thermal_workload_name(args, n, ppc=8):
+    """The config.workload string of the thermal benchmark (both arms)."""
+    return (f"thermal_{args.shape}_{n}: {n}^3 periodic cells, electrons {ppc} ppc "
+            f"({n ** 3 * ppc} particles/GPU), u_th 0.05c, {args.shape.upper()}, "
+            "dt = 0.5 Courant, neutralising background"
+            + (", energy-conserving gather" if args.gather == "energy" else ""))
+
+
 def run_reference(args, rank):
     """The FP64 oracle as it stands, on this host's cores: each step is one
     full PIC step of a bounded sample (16^3 box, same recipe)."""
@@ -701,7 +706,8 @@ def run_reference(args, rank):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": f"thermal_tsc_{args.n} (sampled: {n}^3 box per step)"},
+            "config": {"workload": thermal_workload_name(args, args.n),
+                       "form": "FP64 CPU oracle, one host thread; each step a bounded sample (see cpu_baseline)"},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
