@@ -1,6 +1,8 @@
 """Host logic of bench.py (no GPU): the committed push-kernel profile is
 read only while the kernel source still has the hash it was taken on, and
-its per-particle figures parse."""
+its per-particle figures parse; the reference arm (the FP64 oracle on the
+host) prints the contract's JSON line."""
+import argparse
 import hashlib
 import os
 
@@ -58,3 +60,25 @@ def test_missing_profile_gives_nones(tmp_path, monkeypatch):
 def test_shape_table(shape):
     bench = _bench()
     assert bench.SHAPE[shape] in (1, 2, 3)
+
+
+def test_reference_arm_prints_the_contract_line():
+    """bench.py --impl reference runs the oracle on the host and prints one
+    JSON line with the measured arm's metric, unit and config.workload."""
+    import json
+    import subprocess
+    import sys
+
+    bench = _bench()
+    out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "1"],
+                         cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
+    assert d["higher_is_better"] is True and d["value"] > 0
+    args = argparse.Namespace(shape="tsc", gather="momentum")
+    assert d["config"]["workload"] == bench.thermal_workload_name(args, 256)
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
