@@ -61,11 +61,12 @@ def measured_hbm():
 
 
 def push_profile():
-    """Per-particle DRAM bytes, shared-memory wavefronts and FP32 thread
-    instructions of the push kernel from the committed ncu summary (thermal
-    TSC, 8x4x4 supercells, 256 threads), or Nones when the summary is absent or
-    the kernel source changed since the counters were taken."""
-    none = {"tpp": None, "wpp": None, "fpp": None}
+    """Per-particle DRAM bytes, L1 data-pipe wavefronts (shared memory and
+    global LSU traffic; shared only when the summary lacks them) and FP32
+    operations of the push kernel from the committed ncu summary (thermal
+    TSC, 8x4x4 supercells, 256 threads), or Nones when the summary is absent
+    or the kernel source changed since the counters were taken."""
+    none = {"tpp": None, "wpp": None, "fpp": None, "wkind": None}
     try:
         with open(PUSH_KERNEL_SRC, "rb") as f:
             sha = hashlib.sha256(f.read()).hexdigest()
@@ -77,7 +78,10 @@ def push_profile():
                     vals[k.strip()] = v.strip().strip("`")
         if vals.get("k_push.cu sha256") != sha:
             return none
-        return {"tpp": float(vals["dram bytes per particle"]), "wpp": float(vals["shared wavefronts per particle"]),
+        lsu = "l1 data-pipe wavefronts per particle"
+        return {"tpp": float(vals["dram bytes per particle"]),
+                "wpp": float(vals[lsu] if lsu in vals else vals["shared wavefronts per particle"]),
+                "wkind": "l1" if lsu in vals else "smem",
                 "fpp": float(vals["fp32 operations per particle"]) if "fp32 operations per particle" in vals
                 else None}
     except Exception:  # noqa: BLE001
@@ -139,9 +143,10 @@ class ClockSampler:
 # ----------------------------------------------------------------------------- ours
 
 def binding_roofline(result, npart):
-    """The roofline that binds the TSC push kernel: shared-memory wavefronts
-    (ncu count per particle from the committed profile) per second against
-    one wavefront per cycle per SM at the SM clock sampled during the run."""
+    """The roofline that binds the TSC push kernel: L1 data-pipe wavefronts
+    (shared memory plus global LSU traffic; ncu count per particle from the
+    committed profile) per second against one wavefront per cycle per SM at
+    the SM clock sampled during the run."""
     wpp = result.get("wpp")
     mhz = (result.get("clocks") or {}).get("sm_mhz")
     if not wpp or not mhz:
@@ -154,7 +159,8 @@ def binding_roofline(result, npart):
         return None
     achieved = wpp * npart / (result["push_ms"] * 1e-3) / 1e9
     peak = nsm * mhz * 1e6 / 1e9
-    return {"bound": "smem", "achieved": achieved, "peak": peak, "unit": "G wavefronts/s",
+    return {"bound": "l1_data_pipe" if result.get("wkind") == "l1" else "smem", "achieved": achieved,
+            "peak": peak, "unit": "G wavefronts/s",
             "frac": achieved / peak, "kernel": "k_push_deposit",
             "per_particle": wpp, "peak_source": f"1 wavefront/clk/SM x {nsm} SMs x {mhz:.0f} MHz sampled"}
 
@@ -384,11 +390,13 @@ def run_ours(args, rank, world, dist):
     achieved = push_bytes / (push_ms * 1e-3) / 1e9
     # the committed counters hold for the configuration they were taken on
     prof = push_profile() if (args.shape == "tsc" and args.gather == "momentum" and tuple(sc) == (8, 4, 4)
-                              and threads in (0, 256)) else {"tpp": None, "wpp": None, "fpp": None}
+                              and threads in (0, 256)) else {"tpp": None, "wpp": None, "fpp": None,
+                                                             "wkind": None}
     tpp = prof["tpp"]
     result.update(value=value, step_ms=step_ms_max, push_ms=push_ms, frames_ms=frames_ms,
                   yee_ms=yee_ms, graph=graph, kernels=kernels, achieved=achieved,
                   traffic=None if tpp is None else tpp * npart, clocks=clk.summary(), wpp=prof["wpp"],
+                  wkind=prof["wkind"],
                   fpp=prof["fpp"])
     log(f"[rank {rank}] mixed: push {push_ms:.3f} ms, frames {frames_ms:.3f} ms, yee {yee_ms:.3f} ms,"
         f" step {step_ms:.3f} ms, graph={graph}")

@@ -32,6 +32,7 @@ def test_committed_profile_has_every_figure():
     assert len(vals["k_push.cu sha256"]) == 64
     assert 60.0 < float(vals["dram bytes per particle"]) < 80.0   # 64.5 B algorithmic
     assert 5.0 < float(vals["shared wavefronts per particle"]) < 40.0
+    assert float(vals["shared wavefronts per particle"]) < float(vals["l1 data-pipe wavefronts per particle"]) < 40.0
     assert 100.0 < float(vals["fp32 operations per particle"]) < 3000.0
 
 
@@ -45,15 +46,18 @@ def test_profile_is_used_only_for_the_kernel_it_was_taken_on(tmp_path, monkeypat
                   f"- shared wavefronts per particle: `17.0`\n- fp32 operations per particle: `670`\n")
     monkeypatch.setattr(bench, "PUSH_KERNEL_SRC", str(src))
     monkeypatch.setattr(bench, "TRAFFIC_SUMMARY", str(md))
-    assert bench.push_profile() == {"tpp": 64.5, "wpp": 17.0, "fpp": 670.0}
+    assert bench.push_profile() == {"tpp": 64.5, "wpp": 17.0, "fpp": 670.0, "wkind": "smem"}
+    # the L1 data-pipe count, when present, is the one the binding roofline uses
+    md.write_text(md.read_text() + "- l1 data-pipe wavefronts per particle: `18.0`\n")
+    assert bench.push_profile() == {"tpp": 64.5, "wpp": 18.0, "fpp": 670.0, "wkind": "l1"}
     src.write_bytes(b"// a changed kernel\n")
-    assert bench.push_profile() == {"tpp": None, "wpp": None, "fpp": None}
+    assert bench.push_profile() == {"tpp": None, "wpp": None, "fpp": None, "wkind": None}
 
 
 def test_missing_profile_gives_nones(tmp_path, monkeypatch):
     bench = _bench()
     monkeypatch.setattr(bench, "TRAFFIC_SUMMARY", str(tmp_path / "absent.md"))
-    assert bench.push_profile() == {"tpp": None, "wpp": None, "fpp": None}
+    assert bench.push_profile() == {"tpp": None, "wpp": None, "fpp": None, "wkind": None}
 
 
 @pytest.mark.parametrize("shape", ["tsc", "cic", "pcs"])
