@@ -49,7 +49,7 @@ typedef enum {
     PIC_ERR_OOM = 3,        /* the device allocator returned NULL */
     PIC_ERR_CUDA = 4,       /* a CUDA runtime call failed (message in pic_last_error) */
     PIC_ERR_FRAME_POOL = 5, /* the frame pool ran out of free frames during a step */
-    PIC_ERR_TIMEOUT = 6,    /* a bounded device-side wait gave up */
+    PIC_ERR_TIMEOUT = 6,    /* a bounded device-side wait gave up (reserved: no kernel waits today) */
     PIC_ERR_STATE = 7,      /* the context is poisoned by an earlier error */
     PIC_ERR_CAPACITY = 8,   /* the per-step buffer of particles changing supercell overflowed */
     PIC_ERR_PARTICLE = 9    /* a particle produced a non-finite momentum or position */
