@@ -100,7 +100,7 @@ typedef struct {
     int32_t track_ids;      /* nonzero: carry a particle id (load order) through the frames */
     int32_t use_graph;      /* nonzero: pic_step replays a captured CUDA graph of one step */
     int32_t sort_every;     /* mixed form: every this many steps the push counting-sorts each frame
-                               list by nearest node (TSC) / cell (CIC) and writes it back in that
+                               list by nearest node (TSC) / cell (CIC, PCS) and writes it back in that
                                order; the steps between push the lists in stored order; 0 = 4,
                                1 = sort on every step (results agree up to FP32 summation order) */
     int64_t pool_frames;    /* frame-pool capacity (mixed); 0 = sized at the first step from the load */
