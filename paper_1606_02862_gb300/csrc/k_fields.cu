@@ -160,12 +160,21 @@ __global__ void __launch_bounds__(256) k_yee_b(const YeeArgs a)
     float* __restrict__ Bz = b.B + 2 * pc;
     const int z0 = c.z * kYeeZ;
     float cx[kYeeZ], cy[kYeeZ], cz[kYeeZ], bx[kYeeZ], by[kYeeZ], bz[kYeeZ];
+    // Ex, Ey one plane up are the next cell's own values (the thread's cells
+    // are stacked in z): kYeeZ + 1 planes of them, loaded once
+    float exs[kYeeZ + 1], eys[kYeeZ + 1];
+#pragma unroll
+    for (int q = 0; q <= kYeeZ; ++q) {
+        const int64_t i = pidx<G>(b, c.x, c.y, z0 + q);
+        exs[q] = __ldg(Ex + i);
+        eys[q] = __ldg(Ey + i);
+    }
 #pragma unroll
     for (int q = 0; q < kYeeZ; ++q) {
         const int64_t i = pidx<G>(b, c.x, c.y, z0 + q);
-        const float ex = __ldg(Ex + i), ey = __ldg(Ey + i), ez = __ldg(Ez + i);
-        cx[q] = (__ldg(Ez + i + sy) - ez) * a.ih[1] - (__ldg(Ey + i + sz) - ey) * a.ih[2];
-        cy[q] = (__ldg(Ex + i + sz) - ex) * a.ih[2] - (__ldg(Ez + i + sx) - ez) * a.ih[0];
+        const float ex = exs[q], ey = eys[q], ez = __ldg(Ez + i);
+        cx[q] = (__ldg(Ez + i + sy) - ez) * a.ih[1] - (eys[q + 1] - ey) * a.ih[2];
+        cy[q] = (exs[q + 1] - ex) * a.ih[2] - (__ldg(Ez + i + sx) - ez) * a.ih[0];
         cz[q] = (__ldg(Ey + i + sx) - ey) * a.ih[0] - (__ldg(Ex + i + sy) - ex) * a.ih[1];
         bx[q] = Bx[i];
         by[q] = By[i];
@@ -238,6 +247,12 @@ __global__ void __launch_bounds__(256, 4) k_yee_e(const YeeArgs a)
     const int nx = images(c.x, b.nx, G, GuardsOf<G>::hx, ix);
     const int ny = images(c.y, b.ny, G, GuardsOf<G>::hyz, iy);
     float jx[kYeeZ], jy[kYeeZ], jz[kYeeZ], cx[kYeeZ], cy[kYeeZ], cz[kYeeZ], ex[kYeeZ], ey[kYeeZ], ez[kYeeZ];
+    float bxs[kYeeZ + 1], bys[kYeeZ + 1];
+    {
+        const int64_t i0 = pidx<G>(b, c.x, c.y, z0 - 1);
+        bxs[0] = __ldg(Bx + i0);
+        bys[0] = __ldg(By + i0);
+    }
 #pragma unroll
     for (int q = 0; q < kYeeZ; ++q) {
         const int64_t i = pidx<G>(b, c.x, c.y, z0 + q);
@@ -259,9 +274,12 @@ __global__ void __launch_bounds__(256, 4) k_yee_e(const YeeArgs a)
                         jy[q] += J[pc + g];
                         jz[q] += J[2 * pc + g];
                     }
-        const float bxv = __ldg(Bx + i), byv = __ldg(By + i), bzv = __ldg(Bz + i);
-        cx[q] = (bzv - __ldg(Bz + i - sy)) * a.ih[1] - (byv - __ldg(By + i - sz)) * a.ih[2];
-        cy[q] = (bxv - __ldg(Bx + i - sz)) * a.ih[2] - (bzv - __ldg(Bz + i - sx)) * a.ih[0];
+        // Bx, By one plane down: the previous cell's own values (cells stacked in z)
+        bxs[q + 1] = __ldg(Bx + i);
+        bys[q + 1] = __ldg(By + i);
+        const float bxv = bxs[q + 1], byv = bys[q + 1], bzv = __ldg(Bz + i);
+        cx[q] = (bzv - __ldg(Bz + i - sy)) * a.ih[1] - (byv - bys[q]) * a.ih[2];
+        cy[q] = (bxv - bxs[q]) * a.ih[2] - (bzv - __ldg(Bz + i - sx)) * a.ih[0];
         cz[q] = (byv - __ldg(By + i - sx)) * a.ih[0] - (bxv - __ldg(Bx + i - sy)) * a.ih[1];
         ex[q] = Ex[i];
         ey[q] = Ey[i];
