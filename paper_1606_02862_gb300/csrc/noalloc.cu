@@ -5,15 +5,17 @@
 //   W = sum over cells of (E^2 + B^2) / 2 * cell_volume,
 // from device arrays the caller owns, and keeps its per-block partial sums
 // in the file-scope array g_partials below instead of allocating them.  It
-// serves callers that cannot call cudaMalloc when they need the number: code
-// that runs while a stream is being captured into a CUDA graph (allocation
-// is not permitted there), and hosts that give a library only memory they
-// reserved up front.
+// serves callers that cannot call cudaMalloc when they need the number:
+// hosts that give a library only memory they reserved up front, and code
+// running where the host's rules forbid a device allocation at that point.
 //
 // The array is shared by every call on a device and keeps the last call's
 // contents.  Each call writes every partial it later reads, so nothing has to
 // start at zero, but calls whose work overlaps on the GPU (two streams, or
-// two host threads) race on it: order them on one stream.
+// two host threads) race on it: order them on one stream.  Its device
+// address is looked up once per device and kept for the life of the process;
+// a device reset (cudaDeviceReset) makes that address stale and is not
+// supported between calls.
 #include "pic.h"
 
 #include <cuda_runtime.h>
@@ -123,10 +125,17 @@ extern "C" pic_status pic_field_energy_noalloc(const double* E, const double* B,
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int64_t n3 = 3 * ncells;
     const int nblk = (int)((n3 + kSpan - 1) / kSpan);  // <= kMaxBlocks for ncells <= kMaxCells
-    if (nblk > 0)
-        k_energy_partials<<<nblk, kThreads, 0, s>>>(E, B, n3, partials);
-    k_energy_final<<<1, 1024, 0, s>>>(partials, nblk, 0.5 * cell_volume, out);
-    if (cudaGetLastError() != cudaSuccess)
+    // each launch is judged by its own return code: an error that earlier,
+    // unrelated calls left pending is neither reported here nor cleared
+    if (nblk > 0) {
+        void* args[] = {(void*)&E, (void*)&B, (void*)&n3, (void*)&partials};
+        if (cudaLaunchKernel((const void*)k_energy_partials, dim3(nblk), dim3(kThreads), args, 0, s) !=
+            cudaSuccess)
+            return PIC_ERR_CUDA;
+    }
+    const double half_vol = 0.5 * cell_volume;
+    void* fargs[] = {(void*)&partials, (void*)&nblk, (void*)&half_vol, (void*)&out};
+    if (cudaLaunchKernel((const void*)k_energy_final, dim3(1), dim3(1024), fargs, 0, s) != cudaSuccess)
         return PIC_ERR_CUDA;
     return PIC_OK;
 }

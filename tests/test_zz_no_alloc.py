@@ -1,9 +1,8 @@
 """pic_field_energy_noalloc: the field energy without any device allocation.
 
-Callers that cannot allocate device memory when they need the number (code
-inside a CUDA stream capture, hosts that hand out only pre-reserved memory)
-get the same FP64 field energy as pic_diagnostics out[0] from arrays they
-own.  The test builds a field state with a context, copies E and B to
+Callers that cannot allocate device memory when they need the number (hosts
+that hand out only pre-reserved memory) get the same FP64 field energy as
+pic_diagnostics out[0] from arrays they own.  The test builds a field state with a context, copies E and B to
 device tensors, and calls the entry point twice in a row through the C ABI
 -- once on the state, once on a scaled copy -- checking each result against
 the context's own reduction.  This file sorts last so that a run stopping at
