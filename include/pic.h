@@ -93,10 +93,25 @@ enum {
 /* Field selectors for pic_write_fields / pic_read_fields. */
 enum { PIC_FIELD_E = 0, PIC_FIELD_B = 1, PIC_FIELD_J = 2, PIC_FIELD_RHO = 3 };
 
+/*
+ * Supercell shape and threads per supercell (mixed form; Sec. 2.1: a
+ * supercell is the unit a block of threads works on, and its shape is a
+ * tuning parameter of the code).  Left 0, they are tuned by the library:
+ * before the first step it times every configuration the push kernel is
+ * built for that fits the boxes (sc 0,0,0: supercell shapes and thread
+ * counts; threads_per_sc 0 with a given sc: thread counts) on the loaded
+ * state itself -- push and frame maintenance of 3 steps after 2 warm-up
+ * steps each, in side contexts on the context's stream and allocator -- and
+ * moves the context into the fastest.  The result is kept for the process
+ * and reused for states of the same kind (box sizes, species, particles per
+ * cell).  Until then particles sit in 4 x 4 x 4 supercells.  pic_info
+ * reports the configuration in use.  A subdomain context
+ * (pic_set_subdomain) keeps the configuration it was created with.
+ */
 typedef struct {
     int32_t precision;      /* PIC_PRECISION_* */
-    int32_t sc[3];          /* supercell edge in cells (mixed form); 0,0,0 = 4 x 4 x 4 */
-    int32_t threads_per_sc; /* CUDA threads per supercell work item (mixed form); 0 = cells per supercell */
+    int32_t sc[3];          /* supercell edge in cells (mixed form); 0,0,0 = tuned (see above) */
+    int32_t threads_per_sc; /* CUDA threads per supercell work item (mixed form); 0 = tuned */
     int32_t track_ids;      /* nonzero: carry a particle id (load order) through the frames */
     int32_t use_graph;      /* nonzero: pic_step replays a captured CUDA graph of one step */
     int32_t sort_every;     /* mixed form: every this many steps the push counting-sorts each frame
@@ -290,13 +305,19 @@ pic_status pic_stage_times(pic_ctx* ctx, double ms[4], int64_t* nsteps_out);
  * pic_info -- one integer property of the context into *out:
  *   PIC_INFO_GRAPH_ACTIVE    1 if pic_step replays captured CUDA graphs (mixed form,
  *                            after the first step), else 0;
- *   PIC_INFO_KERNELS_PER_STEP number of libpic kernel launches one step makes;
+ *   PIC_INFO_KERNELS_PER_STEP number of libpic kernel launches one step makes (for a
+ *                            subdomain slab: its stages and its halo / migrant calls);
  *   PIC_INFO_POOL_FRAMES     frame-pool capacity (mixed form);
  *   PIC_INFO_FRAMES_USED     frames holding particles, read from the device;
  *   PIC_INFO_MOVE_CAPACITY   capacity of the per-step buffer of particles changing supercell;
  *   PIC_INFO_STEPS           steps taken since pic_create (the time of E is STEPS * dt);
  *   PIC_INFO_HOST_DIRECT     pic_load_particles / pic_read_particles / pic_read_fields calls
- *                            of the mixed form that converted page-locked host arrays in place.
+ *                            of the mixed form that converted page-locked host arrays in place;
+ *   PIC_INFO_SUPERCELL_X/_Y/_Z, PIC_INFO_THREADS  the supercell edges and threads per
+ *                            supercell the mixed form runs with (chosen by the library's
+ *                            tuner once the first step began, when pic_options left them 0);
+ *   PIC_INFO_TUNE_TRIALS     configurations the tuner timed for this context (0: given in
+ *                            the options, or taken from an earlier tuning in this process).
  */
 enum {
     PIC_INFO_GRAPH_ACTIVE = 0,
@@ -305,18 +326,123 @@ enum {
     PIC_INFO_FRAMES_USED = 3,
     PIC_INFO_MOVE_CAPACITY = 4,
     PIC_INFO_STEPS = 5,
-    PIC_INFO_HOST_DIRECT = 6
+    PIC_INFO_HOST_DIRECT = 6,
+    PIC_INFO_SUPERCELL_X = 7,
+    PIC_INFO_SUPERCELL_Y = 8,
+    PIC_INFO_SUPERCELL_Z = 9,
+    PIC_INFO_THREADS = 10,
+    PIC_INFO_TUNE_TRIALS = 11
 };
 pic_status pic_info(pic_ctx* ctx, int32_t key, int64_t* out);
+
+/*
+ * Domain decomposition of one periodic box into slabs along z (Sec. 2.1:
+ * the simulation domain is split into local domains, one per device, each
+ * a block of supercells; Sec. 1: PIConGPU runs on many GPUs).  Each process
+ * holds one slab as a one-box context; the z faces of the slab exchange
+ * with the neighbouring slabs (below: side 0, above: side 1) instead of
+ * wrapping periodically; x and y stay periodic.  The caller moves the
+ * messages between neighbours (NCCL, MPI, device copies) and runs the step
+ * stage by stage:
+ *   PUSH; exchange J (pic_halo_*) and migrants (pic_migrants_*); FRAMES;
+ *   B_FIRST; exchange B; E; exchange E; B_SECOND; exchange B.
+ * After pic_write_fields, exchange E and B once before the first step.
+ *
+ * pic_set_subdomain -- make box 0 of a one-box mixed-form context a z slab:
+ *   enable              nonzero: z faces exchange (zero: periodic again);
+ *   migrant_capacity    particles per face per step the migrant messages
+ *                       hold; 0 = two per face cell.  More leavers in one
+ *                       step raise PIC_ERR_CAPACITY;
+ *   id_base             with track_ids: the particles loaded after this call
+ *                       get ids from id_base on (per species), so that the
+ *                       slabs of one box can give every particle its own id
+ *                       (migrants keep theirs).
+ * The slab keeps its own local coordinates: z in [0, nz) (the caller loads
+ * the particles of its slab in those coordinates).  Not with open-y options
+ * (PIC_ERR_ARG).  A subdomain context steps only through pic_step_stage;
+ * pic_step and pic_step_async return PIC_ERR_ARG.  pic_diagnostics out[3]
+ * (the Gauss residual) is taken over nodes at least 3 planes from the z
+ * faces; pic_read_fields(PIC_FIELD_RHO) is exact at those nodes only.
+ */
+typedef struct {
+    int32_t enable;
+    int32_t reserved;
+    int64_t migrant_capacity;
+    int64_t id_base;
+} pic_subdomain;
+pic_status pic_set_subdomain(pic_ctx* ctx, int32_t box, const pic_subdomain* sub);
+
+/*
+ * pic_step_stage -- enqueue one stage of a PIC step on the context's stream
+ * (mixed form), in the order PIC_STAGE_PUSH, _FRAMES, _B_FIRST, _E,
+ * _B_SECOND (step order in the file header):
+ *   PUSH      gather, Boris, move, Esirkepov deposit into a zeroed J,
+ *             in-kernel frame compaction; particles leaving through a
+ *             subdomain z face go to that face's migrant message;
+ *   FRAMES    frame table of the next step, placing of the particles that
+ *             changed supercell (accepted migrants included);
+ *   B_FIRST   B^{n+1/2} = B^n - dt/2 curl E^n;
+ *   E         antenna current (if any), E^{n+1} = E^n + dt (curl B - J);
+ *   B_SECOND  B^{n+1} = B^{n+1/2} - dt/2 curl E^{n+1}, y absorber (if any).
+ * A stage out of order returns PIC_ERR_ARG.  Device conditions surface at
+ * pic_sync.  pic_step_async on a periodic context is the same five stages
+ * with nothing between them.
+ */
+enum {
+    PIC_STAGE_PUSH = 0,
+    PIC_STAGE_FRAMES = 1,
+    PIC_STAGE_B_FIRST = 2,
+    PIC_STAGE_E = 3,
+    PIC_STAGE_B_SECOND = 4
+};
+pic_status pic_step_stage(pic_ctx* ctx, int32_t stage);
+
+/*
+ * Field halos of a subdomain box (FP32, device memory the caller owns):
+ *   which = PIC_FIELD_E or _B: the message to the neighbour on `side` holds
+ *           the interior planes that neighbour keeps as guard planes; the
+ *           message from the neighbour on `side` overwrites this slab's
+ *           guard planes on that face;
+ *   which = PIC_FIELD_J: the message to the neighbour on `side` holds this
+ *           slab's guard planes on that face (current deposited by its
+ *           particles into the neighbour's cells); the message from the
+ *           neighbour on `side` is added into this slab's interior planes
+ *           on that face.
+ * Messages are whole padded planes (x and y guard columns included),
+ * component-major.  pic_halo_floats gives the floats of the message sent
+ * to `side`; the message received from side s has the size of the one the
+ * neighbour sends to side 1 - s.  pic_halo_pack / _unpack enqueue on the
+ * context's stream and return at once; `buf` must stay valid until the
+ * stream reaches the copy.
+ */
+pic_status pic_halo_floats(pic_ctx* ctx, int32_t box, int32_t which, int32_t side, int64_t* nfloats);
+pic_status pic_halo_pack(pic_ctx* ctx, int32_t box, int32_t which, int32_t side, float* buf);
+pic_status pic_halo_unpack(pic_ctx* ctx, int32_t box, int32_t which, int32_t side, const float* buf);
+
+/*
+ * Migrant messages of a subdomain box: the particles that left through the
+ * face `side` in the last PUSH stage, for the neighbour on that side.  A
+ * message is pic_migrant_bytes bytes (device memory the caller owns): a
+ * 16-byte header (int32 count, int32 capacity) and fixed-size records (species,
+ * supercell x and y, cell inside the supercell, FP32 offsets, momentum and
+ * weight, particle id).  pic_migrants_pack copies the message of `side`;
+ * pic_migrants_accept takes the message from the neighbour on `side` (they
+ * enter this slab's supercell row on that face) into the step's arrivals:
+ * call it after PUSH and before FRAMES.  Both enqueue on the context's
+ * stream and return at once.
+ */
+pic_status pic_migrant_bytes(pic_ctx* ctx, int64_t* bytes);
+pic_status pic_migrants_pack(pic_ctx* ctx, int32_t side, void* buf);
+pic_status pic_migrants_accept(pic_ctx* ctx, int32_t side, const void* buf);
 
 /*
  * pic_field_energy_noalloc -- the field energy of pic_diagnostics out[0],
  * sum over cells of (E^2 + B^2) / 2 * cell_volume, computed in FP64 from
  * device arrays the caller owns, without allocating any device memory.
  * The paper has no counterpart: this is a service for callers that cannot
- * call cudaMalloc at the moment they need the number -- code running while a
- * stream is captured into a CUDA graph, where allocation is not allowed, and
- * hosts that hand a library only memory they reserved in advance.
+ * call cudaMalloc at the moment they need the number -- hosts that hand a
+ * library only memory they reserved in advance, and code running where the
+ * host's own rules forbid a device allocation at that point.
  *   E, B         device arrays of 3 * ncells doubles each (component-major,
  *                the layout pic_read_fields returns); read only.
  *   ncells       number of cells, 0 <= ncells <= 44,739,242; larger sizes are
@@ -329,10 +455,13 @@ pic_status pic_info(pic_ctx* ctx, int32_t key, int64_t* out);
  * The partial sums live in a 128 KB array that every device loading the
  * library holds until the process exits.  The first call on a device looks
  * up that array's device address (cudaGetSymbolAddress), so make the first
- * call on each device before any stream capture.  Every call overwrites the
- * partials it reads, but calls that overlap on the GPU (other streams or
- * host threads) share the array and race: order them on one stream.
- * Returns PIC_ERR_ARG for bad arguments, PIC_ERR_CUDA if a launch fails.
+ * call on each device before any stream capture.  The address is kept for
+ * the life of the process: a device reset (cudaDeviceReset) between calls is
+ * not supported.  Every call overwrites the partials it reads, but calls that
+ * overlap on the GPU (other streams or host threads) share the array and
+ * race: order them on one stream.
+ * Returns PIC_ERR_ARG for bad arguments, PIC_ERR_CUDA if one of its own
+ * launches fails (an error left pending by earlier calls is not consumed).
  */
 pic_status pic_field_energy_noalloc(const double* E, const double* B, int64_t ncells,
                                     double cell_volume, double* out, void* stream);

@@ -19,6 +19,7 @@
 // kYeeZ cells along z, box found from a per-box block offset table.
 #include "pic_internal.cuh"
 
+#include <algorithm>
 #include <cmath>
 
 namespace pic {
@@ -257,7 +258,9 @@ __global__ void __launch_bounds__(256, 4) k_yee_e(const YeeArgs a)
     for (int q = 0; q < kYeeZ; ++q) {
         const int64_t i = pidx<G>(b, c.x, c.y, z0 + q);
         int iz[2];
-        const int nz = images(z0 + q, b.nz, G, GuardsOf<G>::hyz, iz);
+        // a subdomain slab's z guards went to its neighbours (and theirs came
+        // in as additions): no z images to fold there
+        const int nz = b.sub_z ? (iz[0] = z0 + q, 1) : images(z0 + q, b.nz, G, GuardsOf<G>::hyz, iz);
         // fold the J guard images into the interior
         jx[q] = 0.f;
         jy[q] = 0.f;
@@ -347,22 +350,81 @@ __global__ void __launch_bounds__(256) k_absorb_y(const BoxDev* boxes, const int
     store_with_images(b, b.B + 2 * pc, c, b.B[2 * pc + i] * fh);
 }
 
-cudaError_t launch_yee_mixed_plan(const YeePlan& p, cudaStream_t st)
+cudaError_t launch_yee_mixed_part(const YeePlan& p, int part, cudaStream_t st)
 {
     YeeArgs a{p.boxes, p.blk_off, p.nboxes, 0.5f * p.dt, {p.ih[0], p.ih[1], p.ih[2]},
               p.step_no, p.dt_d, {p.dx_d[0], p.dx_d[1], p.dx_d[2]}};
     dim3 blk(32, 8);
     auto yb = p.guard == 2 ? k_yee_b<2> : k_yee_b<1>;
     auto ye = p.guard == 2 ? k_yee_e<2> : k_yee_e<1>;
-    yb<<<p.nblocks, blk, 0, st>>>(a);
-    if (p.antenna)
-        k_antenna<<<64, 256, 0, st>>>(a);
-    a.tau = p.dt;
-    ye<<<p.nblocks, blk, 0, st>>>(a);
-    a.tau = 0.5f * p.dt;
-    yb<<<p.nblocks, blk, 0, st>>>(a);
-    if (p.abs_nblocks > 0)
-        k_absorb_y<<<p.abs_nblocks, 256, 0, st>>>(p.boxes, p.abs_off, p.nboxes);
+    if (part == 0) {
+        yb<<<p.nblocks, blk, 0, st>>>(a);
+    } else if (part == 1) {
+        if (p.antenna)
+            k_antenna<<<64, 256, 0, st>>>(a);
+        a.tau = p.dt;
+        ye<<<p.nblocks, blk, 0, st>>>(a);
+    } else {
+        yb<<<p.nblocks, blk, 0, st>>>(a);
+        if (p.abs_nblocks > 0)
+            k_absorb_y<<<p.abs_nblocks, 256, 0, st>>>(p.boxes, p.abs_off, p.nboxes);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_yee_mixed_plan(const YeePlan& p, cudaStream_t st)
+{
+    for (int part = 0; part < 3; ++part) {
+        const cudaError_t e = launch_yee_mixed_part(p, part, st);
+        if (e != cudaSuccess)
+            return e;
+    }
+    return cudaSuccess;
+}
+
+// ------------------------------------------------------------ subdomain halos
+
+// Whole padded planes [p0, p0 + np) of the three components of F and a
+// contiguous buffer [comp][plane][py][px]: mode 0 copies F to buf, 1 buf to
+// F, 2 adds buf into F.  The planes of one component are contiguous in F
+// too, so both sides are read and written in 16-byte pieces (px is a
+// multiple of 4).
+__global__ void k_halo_planes(const BoxDev b, float* F, int p0, int np, float* buf, int mode)
+{
+    const int64_t plane4 = (int64_t)b.px * b.py / 4;
+    const int64_t per_comp = plane4 * np;
+    const int64_t pc4 = padded_cells(b) / 4;
+    float4* F4 = reinterpret_cast<float4*>(F);
+    float4* B4 = reinterpret_cast<float4*>(buf);
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < 3 * per_comp;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int comp = (int)(t / per_comp);
+        const int64_t r = t - comp * per_comp;
+        const int64_t f = comp * pc4 + (int64_t)p0 * plane4 + r;
+        if (mode == 0) {
+            B4[t] = F4[f];
+        } else if (mode == 1) {
+            F4[f] = B4[t];
+        } else {
+            const float4 v = B4[t];
+            float4 u = F4[f];
+            u.x += v.x;
+            u.y += v.y;
+            u.z += v.z;
+            u.w += v.w;
+            F4[f] = u;
+        }
+    }
+}
+
+cudaError_t launch_halo_planes(const BoxDev& b, float* F, int p0, int np, float* buf, int mode,
+                               cudaStream_t st)
+{
+    if (np <= 0)
+        return cudaSuccess;
+    const int64_t n4 = 3 * (int64_t)b.px * b.py / 4 * np;
+    const int blocks = (int)std::min<int64_t>((n4 + 255) / 256, 2048);
+    k_halo_planes<<<blocks, 256, 0, st>>>(b, F, p0, np, buf, mode);
     return cudaGetLastError();
 }
 
@@ -430,7 +492,8 @@ __global__ void k_fields_from_padded(const BoxDev b, const float* F, double* dst
             continue;
         }
         int ix[2], iy[2], iz[2];
-        const int nx = images_x(b, x, ix), ny = images_y(b, y, iy), nz = images_z(b, z, iz);
+        const int nx = images_x(b, x, ix), ny = images_y(b, y, iy);
+        const int nz = b.sub_z ? (iz[0] = z, 1) : images_z(b, z, iz);
         float v = 0.0f;
         for (int k = 0; k < nz; ++k)
             for (int j = 0; j < ny; ++j)
@@ -572,6 +635,10 @@ __global__ void k_diag_gauss(const BoxDev b, const double* rho, double rho_bg, d
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
          t += (int64_t)gridDim.x * blockDim.x) {
         int x = (int)(t % b.nx), y = (int)((t / b.nx) % b.ny), z = (int)(t / ((int64_t)b.nx * b.ny));
+        // a subdomain slab's charge density near its z faces misses the
+        // neighbour's particles: its residual is taken 3 planes inside
+        if (b.sub_z && (z < 3 || z >= b.nz - 3))
+            continue;
         int64_t i = padded_index(b, x, y, z);
         double div = ((double)b.E[i] - (double)b.E[i - 1]) * ih0 +
                      ((double)b.E[pc + i] - (double)b.E[pc + i - b.px]) * ih1 +

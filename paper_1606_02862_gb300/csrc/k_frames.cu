@@ -279,6 +279,53 @@ cudaError_t launch_frame_apply(const StepDev& d, int place_blocks, cudaStream_t 
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------ subdomain migrants
+
+// The migrant message of the neighbouring slab on face `side` of box `box`
+// (a one-box subdomain context): every record joins this step's arrivals
+// (the move buffer) in supercell (sx, sy, row on that face), where the frame
+// plan and k_place then put it like any particle that changed supercell.
+__global__ void k_mig_accept(const StepDev d, int box, int side, const char* msg)
+{
+    const BoxDev b = d.boxes[box];
+    const MigHeader h = *reinterpret_cast<const MigHeader*>(msg);
+    const int n = min(h.count, h.cap);
+    const MigRec* rec = reinterpret_cast<const MigRec*>(msg + sizeof(MigHeader));
+    const int sz = side == 0 ? 0 : b.nscz - 1;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const MigRec r = rec[i];
+        if (r.s < 0 || r.s >= d.nspecies || r.sx < 0 || r.sx >= b.nscx || r.sy < 0 || r.sy >= b.nscy ||
+            r.cell < 0 || r.cell >= d.S) {
+            atomicOr(d.status, ST_PARTICLE);  // a malformed record is dropped
+            continue;
+        }
+        const int L = r.s * d.nsc + b.sc_base + (sz * b.nscy + r.sy) * b.nscx + r.sx;
+        const int m = atomicAdd(d.mv_count, 1);
+        if (m >= d.mv_cap) {
+            atomicOr(d.status, ST_CAPACITY);
+            continue;
+        }
+        d.mv_rank[m] = atomicAdd(d.narrive + L, 1);
+        d.mv_dest[m] = L;
+        d.mv_cell[m] = r.cell;
+        d.mv_ox[m] = r.ox;
+        d.mv_oy[m] = r.oy;
+        d.mv_oz[m] = r.oz;
+        d.mv_ux[m] = r.ux;
+        d.mv_uy[m] = r.uy;
+        d.mv_uz[m] = r.uz;
+        d.mv_w[m] = r.w;
+        if (d.pid)
+            d.mv_pid[m] = r.pid;
+    }
+}
+
+cudaError_t launch_mig_accept(const StepDev& d, int box, int side, const char* msg, cudaStream_t st)
+{
+    k_mig_accept<<<256, 256, 0, st>>>(d, box, side, msg);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------ load / read
 
 // Host particles (FP64, n x 3 global cell coordinates) -> move buffer.  A
@@ -290,7 +337,8 @@ constexpr int kInsertBlock = 256;
 
 __global__ void __launch_bounds__(kInsertBlock) k_insert_convert(const StepDev d, int box, int species, int n,
                                                                  const double* x, const double* u,
-                                                                 const double* w, int id_base)
+                                                                 const double* w, int id_base,
+                                                                 const int64_t* ids)
 {
     __shared__ double sx[3 * kInsertBlock], su[3 * kInsertBlock], sw[kInsertBlock];
     const BoxDev b = d.boxes[box];
@@ -351,17 +399,17 @@ __global__ void __launch_bounds__(kInsertBlock) k_insert_convert(const StepDev d
         d.mv_uz[i] = (float)su[3 * t + 2];
         d.mv_w[i] = (float)wv;
         if (d.mv_pid)
-            d.mv_pid[i] = id_base + i;
+            d.mv_pid[i] = ids ? (int)ids[i] : id_base + i;
     }
 }
 
 cudaError_t launch_insert_convert(const StepDev& d, int box, int species, int64_t n,
                                   const double* x, const double* u, const double* w, int id_base,
-                                  cudaStream_t st)
+                                  const int64_t* ids, cudaStream_t st)
 {
     int blocks = (int)std::min<int64_t>((n + kInsertBlock - 1) / kInsertBlock, 4096);
     if (blocks > 0)
-        k_insert_convert<<<blocks, kInsertBlock, 0, st>>>(d, box, species, (int)n, x, u, w, id_base);
+        k_insert_convert<<<blocks, kInsertBlock, 0, st>>>(d, box, species, (int)n, x, u, w, id_base, ids);
     return cudaGetLastError();
 }
 

@@ -14,11 +14,14 @@
 //      per component at its Yee position, Sec. 4; optionally one order lower
 //      along the component's staggered axes, the energy-conserving variant),
 //      relativistic Boris push, move, then Esirkepov deposition (Sec. 4) into
-//      the shared J tile with shared atomics; particles that leave the
-//      supercell go to the move buffer (or, through a y face of an open-y
-//      box, out of the simulation);
-//   4. compact the frame list (fill the holes the leavers left);
-//   5. add the J tile to the guard-padded global J with 16-byte vector
+//      the shared J tile with shared atomics; the particles that stay go back
+//      to the list compacted (in chunk order, so the leavers' slots close up
+//      as the list is written); particles that leave the supercell collect in
+//      a shared leaver buffer that the CTA hands to the move buffer at its
+//      next work item (or leave through a subdomain slab's z face into a
+//      migrant message, or through a y face of an open-y box out of the
+//      simulation);
+//   4. add the J tile to the guard-padded global J with 16-byte vector
 //      atomics (neighbouring supercells overlap in their guard cells).
 //
 // Esirkepov (2001): with 1D shape factors S0 (old) and S1 (new) on a common
@@ -45,7 +48,9 @@
 //     (no cancellation in FP32); 54 (TSC) / 12 (CIC) / 144 (PCS) shared
 //     atomics, no branches;
 //   general: the rest (a few percent of particles) are listed and deposited
-//     on a 4-node (CIC, TSC) or 5-node (PCS) window after the common loop:
+//     on a 4-node (CIC, TSC) or 5-node (PCS) window: set aside (up to
+//     kGenDefer per list) and deposited lane-parallel after the list's last
+//     chunk with their own fixed-point scale; beyond that, with their chunk:
 //     whole groups of 32 lane-parallel, the leftover moves one per warp with
 //     all 32 lanes on the move's current lines.
 // The shared tiles use a row pitch of 4 mod 8 floats, so that rows are
@@ -57,7 +62,13 @@
 
 namespace pic {
 
-constexpr int kHoleCap = 256;
+// General-window moves of a frame list deposited together after its last
+// chunk (more are deposited with their own chunk).
+constexpr int kGenDefer = 64;
+// Particles changing supercell that a CTA collects in shared memory and hands
+// to the move buffer at the start of its next work item (more go straight
+// to the move buffer).
+constexpr int kLeaverBuf = 48;
 // Lane stride of the deposit over the node-sorted chunk: 4 spreads one
 // warp's 54 atomics per particle over the banks better than 1 (neighbours
 // share a node) or C / 32 (random over the tile).
@@ -80,6 +91,7 @@ struct Tile {
     static constexpr int PX = (TX % 8 == 4) ? TX : (TX % 8 == 0 ? TX + 4 : ((TX + 3) / 4) * 4);
     static constexpr int N = PX * TY * TZ;  // shared floats per component
     static constexpr int S = LX * LY * LZ;
+    static_assert(PX % 4 == 0 && N % 4 == 0, "tile rows and components are 16-byte aligned");
 };
 
 // ------------------------------------------------------------ shape factors
@@ -532,7 +544,7 @@ __device__ __forceinline__ void warp_exclusive_scan_counts(const int* cnt, int* 
 
 // Particles of one chunk of a frame list, staged in shared memory in list
 // order, plus their counting-sort permutation by nearest node.
-template <int C>
+template <int C, bool PCS>
 struct Stage {
     int cell[C];
     float o[3][C];
@@ -541,7 +553,7 @@ struct Stage {
     int pid[C];   // particle ids (only when tracked)
     int kr[C];    // key << 16 | rank within key
     int perm[C];  // sorted position -> chunk position
-    int brk[C];   // PCS, by push position: bank << 16 | rank within the bank
+    int brk[PCS ? C : 1];  // PCS, by push position: bank << 16 | rank within the bank
 };
 
 // Deposit inputs of the chunk's moves, by sorted position s stored at slot
@@ -588,19 +600,42 @@ constexpr int max_keys()
     return (T::LX + 1) * (T::LY + 1) * (T::LZ + 1);
 }
 
+// General-window moves set aside for one lane-parallel deposit after the
+// last chunk of a frame list (the few of each chunk would otherwise keep one
+// warp busy while the others wait at the chunk's last barrier).
+struct GenDefer {
+    int l[kGenDefer];        // packed local cell, as in Records
+    float o[3][kGenDefer];   // old in-cell offsets
+    float D[3][kGenDefer];   // displacement in cells
+    float w[kGenDefer];      // weight
+};
+
+// Particles leaving the supercell, bound for the move buffer.
+struct LeaverBuf {
+    int dest[kLeaverBuf];  // destination list
+    int cell[kLeaverBuf];  // cell inside the destination supercell
+    float o[3][kLeaverBuf];
+    float u[3][kLeaverBuf];
+    float w[kLeaverBuf];
+    int pid[kLeaverBuf];
+};
+
 template <class T, int NT>
 struct SharedState {
     static constexpr int C = 2 * NT < 256 ? 2 * NT : 256;  // chunk: at most 256 particles
-    Stage<C> st;
+    static constexpr int NQ = C / NT;                       // particles per thread and chunk
+    Stage<C, T::G == 2> st;
     Records<C> rec;
+    GenDefer gd;
+    LeaverBuf lv;
     int hist[max_keys<T>()];
     int off[max_keys<T>()];
-    int holes[kHoleCap];
-    int src[kHoleCap];
-    int item, any, nholes, nhead, nsrc;
+    unsigned alive[NQ * NT / 32];  // per warp and pass: ballot of the pushed particles that stay
+    int item, any, nlv, lv_base;
     int ngen[2];             // general-window moves of the chunk
     unsigned bound_bits[2];  // float bits of the chunk's largest |jcoef w D|
-    int bh[32];              // PCS: moves of the chunk per bank of their window origin
+    unsigned gd_bound_bits;  // float bits of the largest |jcoef w D| of the set-aside moves
+    int bh[T::G == 2 ? 32 : 1];  // PCS: moves of the chunk per bank of their window origin
 };
 
 // Bank of the common-window origin of a PCS particle in local cell `cell`
@@ -735,21 +770,20 @@ struct GenWin {
     }
 };
 
-// General window (GenWin) on every axis.
-template <class T, int SHAPE, int C>
-__device__ __forceinline__ void deposit_general(int* sJi, const Records<C>& r, int s, const float jc[3],
-                                                float scale)
+// General window (GenWin) on every axis, for the move of packed local cell
+// l, old offsets o and displacement D (in cells) of a particle of weight w.
+template <class T, int SHAPE>
+__device__ __forceinline__ void deposit_general_move(int* sJi, int l, const float ov[3], const float Dv[3],
+                                                     float w, const float jc[3], float scale)
 {
     using W = GenWin<SHAPE>;
     constexpr int M = W::M;
-    const int e = rslot(s);
-    const int l = r.l[e];
     const int lc[3] = {l & 0xff, (l >> 8) & 0xff, (l >> 16) & 0xff};  // node cell-1 sits at tile index lc
     float S0[3][M], DS[3][M];
     int b[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        const float o = r.o[a][e], D = r.D[a][e];
+        const float o = ov[a], D = Dv[a];
         const int f = W::first(o, D);
         b[a] = lc[a] + f;
 #pragma unroll
@@ -759,9 +793,28 @@ __device__ __forceinline__ void deposit_general(int* sJi, const Records<C>& r, i
             DS[a][k] = W::dS(d0, D);
         }
     }
-    const float ws = r.w[e] * scale;
+    const float ws = w * scale;
     deposit_window<M, T::PX, T::TY, T::N, SHAPE == 3>(sJi, b, S0[0], S0[1], S0[2], DS[0], DS[1], DS[2], jc[0] * ws,
                                           jc[1] * ws, jc[2] * ws);
+}
+
+// The general-window move at sorted position s of the chunk's records.
+template <class T, int SHAPE, int C>
+__device__ __forceinline__ void deposit_general(int* sJi, const Records<C>& r, int s, const float jc[3],
+                                                float scale)
+{
+    const int e = rslot(s);
+    const float o[3] = {r.o[0][e], r.o[1][e], r.o[2][e]};
+    const float D[3] = {r.D[0][e], r.D[1][e], r.D[2][e]};
+    deposit_general_move<T, SHAPE>(sJi, r.l[e], o, D, r.w[e], jc, scale);
+}
+
+// Bound on the current terms of one move (see push_one).
+template <int SHAPE>
+__device__ __forceinline__ float move_bound(const float jc[3], float w, float Dx, float Dy, float Dz)
+{
+    const float tmax = SHAPE == 2 ? 0.5625f * 1.001f : (SHAPE == 3 ? (4.0f / 9.0f) * 1.001f : 1.0f);
+    return tmax * fabsf(w) * fmaxf(fmaxf(fabsf(jc[0] * Dx), fabsf(jc[1] * Dy)), fabsf(jc[2] * Dz));
 }
 
 // General window of one move, deposited by a whole warp (all 32 lanes
@@ -859,13 +912,14 @@ __device__ __forceinline__ void store_part(const StepDev& d, int64_t idx, const 
 // Pushes one particle (gather, Boris, move) and writes its deposit record
 // at slot `slot` of the chunk; returns its bound |jcoef_d w D_d| on the
 // current terms.  A particle that stays in the supercell gets its new cell,
-// offsets and momentum in q; a leaver goes to the move buffer (its id read
-// from pidp when ids are tracked), q.cell becomes -1 and its list slot p
-// joins the hole list.
+// offsets and momentum in q; a leaver goes to the CTA's leaver buffer (or,
+// when that is full, straight to the move buffer), to a neighbouring slab's
+// migrant message, or out of an open-y box; its id is `pid` when ids are
+// tracked, and q.cell becomes -1.
 template <class T, int SHAPE, int NT>
 __device__ __forceinline__ float push_one(const StepDev& d, const SpeciesDev& sp, int s, const BoxDev& bx,
                                          int scx, int scy, int scz, const float* sF,
-                                         SharedState<T, NT>& sh, Part& q, const int* pidp, int p,
+                                         SharedState<T, NT>& sh, Part& q, int pid,
                                          int slot, int cb, unsigned& my_status)
 {
     constexpr int LX = T::LX, LY = T::LY, LZ = T::LZ, N = T::N, PX = T::PX, TY = T::TY;
@@ -886,7 +940,7 @@ __device__ __forceinline__ float push_one(const StepDev& d, const SpeciesDev& sp
     // TSC and PCS: two components per packed FP32 instruction; CIC (8 terms
     // a component) keeps the scalar form, which measured faster there
     float Ex, Ey, Ez, Bx, By, Bz;
-    if (SHAPE != 1) {
+    if constexpr (SHAPE != 1) {
         const float2 Exy = gather_pair<NW, PX, TY>(sF + 0 * N, ax.bh, ay.bi, az.bi, ax.wh, ay.wi, az.wi,
                                                    sF + 1 * N, ax.bi, ay.bh, az.bi, ax.wi, ay.wh, az.wi);
         const float2 EzBx = gather_pair<NW, PX, TY>(sF + 2 * N, ax.bi, ay.bi, az.bh, ax.wi, ay.wi, az.wh,
@@ -946,9 +1000,7 @@ __device__ __forceinline__ float push_one(const StepDev& d, const SpeciesDev& sp
     // bound on every current term of this particle: |jcoef_d w P| with |P| <= |D_d|
     // (P is a difference of cumulative shape sums, whose slope is at most 1),
     // times |T| <= (max S)^2: 9/16 for TSC (S <= 3/4), 4/9 for PCS (S <= 2/3), 1 for CIC
-    const float tmax = SHAPE == 2 ? 0.5625f * 1.001f : (SHAPE == 3 ? (4.0f / 9.0f) * 1.001f : 1.0f);
-    const float bnd = tmax * fabsf(w) * fmaxf(fmaxf(fabsf(sp.jcoef[0] * Dx), fabsf(sp.jcoef[1] * Dy)),
-                                              fabsf(sp.jcoef[2] * Dz));
+    const float bnd = move_bound<SHAPE>(sp.jcoef, w, Dx, Dy, Dz);
 
     // new cell and offsets
     const float fx_ = floorf(x1), fy_ = floorf(y1), fz_ = floorf(z1);
@@ -973,57 +1025,145 @@ __device__ __forceinline__ float push_one(const StepDev& d, const SpeciesDev& sp
         // supercell (periodic within the box), or, through a y face of an
         // open-y box, out of the simulation
         int tsx = scx + dsx, tsy = scy + dsy, tsz = scz + dsz;
-        if (!(bx.oy.open_y && (tsy < 0 || tsy >= bx.nscy))) {
+        if (bx.sub_z && (tsz < 0 || tsz >= bx.nscz)) {
+            // through a z face of a subdomain slab: into that face's migrant
+            // message for the neighbouring slab
+            tsx += tsx < 0 ? bx.nscx : (tsx >= bx.nscx ? -bx.nscx : 0);
+            tsy += tsy < 0 ? bx.nscy : (tsy >= bx.nscy ? -bx.nscy : 0);
+            char* msg = d.mig + (tsz < 0 ? 0 : d.mig_bytes);
+            const int m = atomicAdd(&reinterpret_cast<MigHeader*>(msg)->count, 1);
+            if (m < d.mig_cap) {
+                MigRec r;
+                r.s = s;
+                r.sx = tsx;
+                r.sy = tsy;
+                r.cell = (nlx - dsx * LX) + LX * ((nly - dsy * LY) + LY * (nlz - dsz * LZ));
+                r.ox = nox;
+                r.oy = noy;
+                r.oz = noz;
+                r.ux = ux;
+                r.uy = uy;
+                r.uz = uz;
+                r.w = w;
+                r.pid = pid;
+                int4* dst = reinterpret_cast<int4*>(msg + sizeof(MigHeader) + (int64_t)m * sizeof(MigRec));
+                const int4* src = reinterpret_cast<const int4*>(&r);
+                dst[0] = src[0];
+                dst[1] = src[1];
+                dst[2] = src[2];
+            } else {
+                my_status |= ST_CAPACITY;
+            }
+        } else if (!(bx.oy.open_y && (tsy < 0 || tsy >= bx.nscy))) {
             tsx += tsx < 0 ? bx.nscx : (tsx >= bx.nscx ? -bx.nscx : 0);
             tsy += tsy < 0 ? bx.nscy : (tsy >= bx.nscy ? -bx.nscy : 0);
             tsz += tsz < 0 ? bx.nscz : (tsz >= bx.nscz ? -bx.nscz : 0);
             const int dest_sc = bx.sc_base + (tsz * bx.nscy + tsy) * bx.nscx + tsx;
             const int dest_cell = (nlx - dsx * LX) + LX * ((nly - dsy * LY) + LY * (nlz - dsz * LZ));
             const int destL = s * d.nsc + dest_sc;
-            const int m = warp_aggregated_add(d.mv_count);
-            if (m < d.mv_cap) {
-                d.mv_rank[m] = atomicAdd(d.narrive + destL, 1);
-                d.mv_dest[m] = destL;
-                d.mv_cell[m] = dest_cell;
-                d.mv_ox[m] = nox;
-                d.mv_oy[m] = noy;
-                d.mv_oz[m] = noz;
-                d.mv_ux[m] = ux;
-                d.mv_uy[m] = uy;
-                d.mv_uz[m] = uz;
-                d.mv_w[m] = w;
-                if (d.pid)
-                    d.mv_pid[m] = *pidp;
+            const int k = atomicAdd(&sh.nlv, 1);
+            if (k < kLeaverBuf) {
+                // handed to the move buffer at the CTA's next work item, so
+                // that no warp waits here for a global atomic's reply
+                sh.lv.dest[k] = destL;
+                sh.lv.cell[k] = dest_cell;
+                sh.lv.o[0][k] = nox;
+                sh.lv.o[1][k] = noy;
+                sh.lv.o[2][k] = noz;
+                sh.lv.u[0][k] = ux;
+                sh.lv.u[1][k] = uy;
+                sh.lv.u[2][k] = uz;
+                sh.lv.w[k] = w;
+                sh.lv.pid[k] = pid;
             } else {
-                my_status |= ST_CAPACITY;
+                const int m = warp_aggregated_add(d.mv_count);
+                if (m < d.mv_cap) {
+                    d.mv_rank[m] = atomicAdd(d.narrive + destL, 1);
+                    d.mv_dest[m] = destL;
+                    d.mv_cell[m] = dest_cell;
+                    d.mv_ox[m] = nox;
+                    d.mv_oy[m] = noy;
+                    d.mv_oz[m] = noz;
+                    d.mv_ux[m] = ux;
+                    d.mv_uy[m] = uy;
+                    d.mv_uz[m] = uz;
+                    d.mv_w[m] = w;
+                    if (d.pid)
+                        d.mv_pid[m] = pid;
+                } else {
+                    my_status |= ST_CAPACITY;
+                }
             }
         }
         q.cell = -1;
-        const int h = atomicAdd(&sh.nholes, 1);
-        if (h < kHoleCap)
-            sh.holes[h] = p;
     }
     return bnd;
+}
+
+// The CTA's collected leavers into the move buffer: one reservation, then
+// every leaver's rank among the arrivals of its destination list (all
+// threads converged; sh.nlv stable since the last block barrier).
+template <class T, int NT>
+__device__ __forceinline__ void flush_leavers(const StepDev& d, SharedState<T, NT>& sh, unsigned& my_status)
+{
+    const int n = min(sh.nlv, kLeaverBuf);
+    if (n == 0)
+        return;
+    if (threadIdx.x == 0)
+        sh.lv_base = atomicAdd(d.mv_count, n);
+    __syncthreads();
+    const int base = sh.lv_base;
+    for (int k = threadIdx.x; k < n; k += NT) {
+        const int m = base + k;
+        if (m >= d.mv_cap) {
+            my_status |= ST_CAPACITY;
+            continue;
+        }
+        const int L = sh.lv.dest[k];
+        d.mv_rank[m] = atomicAdd(d.narrive + L, 1);
+        d.mv_dest[m] = L;
+        d.mv_cell[m] = sh.lv.cell[k];
+        d.mv_ox[m] = sh.lv.o[0][k];
+        d.mv_oy[m] = sh.lv.o[1][k];
+        d.mv_oz[m] = sh.lv.o[2][k];
+        d.mv_ux[m] = sh.lv.u[0][k];
+        d.mv_uy[m] = sh.lv.u[1][k];
+        d.mv_uz[m] = sh.lv.u[2][k];
+        d.mv_w[m] = sh.lv.w[k];
+        if (d.pid)
+            d.mv_pid[m] = sh.lv.pid[k];
+    }
 }
 
 // ------------------------------------------------------------ one frame list
 
 // Add the chunk's integer tile (scaled back by inv) into the FP32 tile and
-// clear it; each thread owns its entries, no atomics.
+// clear it; each thread owns its entries (16-byte groups of four; N is a
+// multiple of 4 and both tiles are 16-byte aligned), no atomics.
 template <int N, int NT>
 __device__ __forceinline__ void fold_tile(int* sJi, float* sJf, float inv)
 {
-    for (int v = threadIdx.x; v < 3 * N; v += NT) {
-        const int q = sJi[v];
-        if (q != 0) {
-            sJf[v] += (float)q * inv;
-            sJi[v] = 0;
+    int4* qi = reinterpret_cast<int4*>(sJi);
+    float4* qf = reinterpret_cast<float4*>(sJf);
+    for (int v = threadIdx.x; v < 3 * N / 4; v += NT) {
+        const int4 q = qi[v];
+        if ((q.x | q.y | q.z | q.w) != 0) {
+            float4 f = qf[v];
+            f.x = fmaf((float)q.x, inv, f.x);
+            f.y = fmaf((float)q.y, inv, f.y);
+            f.z = fmaf((float)q.z, inv, f.z);
+            f.w = fmaf((float)q.w, inv, f.w);
+            qf[v] = f;
+            qi[v] = make_int4(0, 0, 0, 0);
         }
     }
 }
 
+// Pushes the frame list of species s in supercell g chunk by chunk and
+// deposits its current into the shared tile; returns the number of its
+// particles that stay (the list's new count; they occupy its first slots).
 template <class T, int SHAPE, int NT>
-__device__ __forceinline__ void push_list(const StepDev& d, const SpeciesDev& sp, int s, int g,
+__device__ __forceinline__ int push_list(const StepDev& d, const SpeciesDev& sp, int s, int g,
                                           const BoxDev& bx, int scx, int scy, int scz,
                                           const float* sF, int* sJi, float* sJf,
                                           SharedState<T, NT>& sh, bool sort_pass, unsigned& my_status)
@@ -1037,7 +1177,10 @@ __device__ __forceinline__ void push_list(const StepDev& d, const SpeciesDev& sp
     const int n = d.count[L];
     const int* ft = d.ftab + d.foff[L];
     auto gidx = [&](int slot) -> int64_t { return (int64_t)ft[slot >> d.log2S] * S + (slot & (S - 1)); };
+    constexpr int NQ = SharedState<T, NT>::NQ, NWARP = NT / 32;
     float prev_inv = 0.0f;
+    int ndef = 0;  // general-window moves set aside in sh.gd
+    int surv = 0;  // particles of the list that stay, written back so far
     // chunk c uses the bound / general-list counters cb = c & 1; the other
     // pair is cleared after the chunk's first barrier (its last readers were
     // the previous chunk's deposits, its next writers come after the next
@@ -1047,6 +1190,7 @@ __device__ __forceinline__ void push_list(const StepDev& d, const SpeciesDev& sp
         const int cn = min(C, n - base);
         if (base > 0)
             fold_tile<N, NT>(sJi, sJf, prev_inv);  // previous chunk; the push below does not touch J
+        int boff = 0;
         if (sort_pass) {
             // stage the chunk (coalesced), key = nearest node (TSC) / cell (CIC),
             // then a counting sort; the pushed particles go back to the list
@@ -1092,79 +1236,81 @@ __device__ __forceinline__ void push_list(const StepDev& d, const SpeciesDev& sp
                 }
             }
             __syncthreads();
-            const int boff = DEAL ? bank_offsets(sh.bh, lane) : 0;
-            // push in sorted order: neighbouring lanes read neighbouring field words
-            for (int s0 = 0; s0 < cn; s0 += NT) {
-                const int sidx = s0 + tid;
-                const int slot = DEAL ? dealt_slot<C>(sh.st.brk, sidx, cn, boff) : sidx;
-                float bnd = 0.0f;
-                if (sidx < cn) {
-                    const int j = sh.st.perm[sidx];
-                    Part q;
-                    q.cell = sh.st.cell[j];
-                    q.o[0] = sh.st.o[0][j];
-                    q.o[1] = sh.st.o[1][j];
-                    q.o[2] = sh.st.o[2][j];
-                    q.u[0] = sh.st.u[0][j];
-                    q.u[1] = sh.st.u[1][j];
-                    q.u[2] = sh.st.u[2][j];
-                    q.w = sh.st.w[j];
-                    bnd = push_one<T, SHAPE, NT>(d, sp, s, bx, scx, scy, scz, sF, sh, q, sh.st.pid + j,
-                                                 base + sidx, slot, cb, my_status);
-                    const int64_t idx = gidx(base + sidx);
-                    store_part(d, idx, q, true);
-                    if (d.pid && q.cell >= 0)
-                        d.pid[idx] = sh.st.pid[j];
-                }
-                const unsigned m = __reduce_max_sync(0xffffffffu, __float_as_uint(bnd));
-                if (lane == 0)
-                    atomicMax(&sh.bound_bits[cb], m);
+            boff = DEAL ? bank_offsets(sh.bh, lane) : 0;
+        } else if (DEAL) {
+            for (int j = tid; j < cn; j += NT) {
+                const int bk = dep_bank<T>(sh.st.cell[j]);
+                sh.st.brk[j] = (bk << 16) | atomicAdd(&sh.bh[bk], 1);
             }
-        } else {
-            // push in stored order (sorted at the last sort pass, a few
-            // particles displaced since): from the stage, which an async copy
-            // filled while the previous chunk deposited, and back to the same
-            // slot of the pool
-            int boff = 0;
-            if (DEAL) {
-                for (int j = tid; j < cn; j += NT) {
-                    const int bk = dep_bank<T>(sh.st.cell[j]);
-                    sh.st.brk[j] = (bk << 16) | atomicAdd(&sh.bh[bk], 1);
-                }
-                __syncthreads();
-                boff = bank_offsets(sh.bh, lane);
+            __syncthreads();
+            boff = bank_offsets(sh.bh, lane);
+        }
+        // push: sort passes in sorted order (neighbouring lanes read
+        // neighbouring field words), the passes between in stored order from
+        // the stage an async copy filled while the previous chunk deposited.
+        // Every read of the chunk's list slots happens before the barrier
+        // below, every write after it.
+        Part qs[NQ];
+        int pids[NQ];
+#pragma unroll
+        for (int r = 0; r < NQ; ++r) {
+            const int sidx = r * NT + tid;
+            const int slot = DEAL ? dealt_slot<C>(sh.st.brk, sidx, cn, boff) : sidx;
+            float bnd = 0.0f;
+            qs[r].cell = -1;
+            if (sidx < cn) {
+                const int j = sort_pass ? sh.st.perm[sidx] : sidx;
+                Part& q = qs[r];
+                q.cell = sh.st.cell[j];
+                q.o[0] = sh.st.o[0][j];
+                q.o[1] = sh.st.o[1][j];
+                q.o[2] = sh.st.o[2][j];
+                q.u[0] = sh.st.u[0][j];
+                q.u[1] = sh.st.u[1][j];
+                q.u[2] = sh.st.u[2][j];
+                q.w = sh.st.w[j];
+                pids[r] = !d.pid ? 0 : (sort_pass ? sh.st.pid[j] : d.pid[gidx(base + sidx)]);
+                bnd = push_one<T, SHAPE, NT>(d, sp, s, bx, scx, scy, scz, sF, sh, q, pids[r], slot, cb,
+                                             my_status);
             }
-            for (int s0 = 0; s0 < cn; s0 += NT) {
-                const int sidx = s0 + tid;
-                const int slot = DEAL ? dealt_slot<C>(sh.st.brk, sidx, cn, boff) : sidx;
-                float bnd = 0.0f;
-                if (sidx < cn) {
-                    const int64_t idx = gidx(base + sidx);
-                    Part q;
-                    q.cell = sh.st.cell[sidx];
-                    q.o[0] = sh.st.o[0][sidx];
-                    q.o[1] = sh.st.o[1][sidx];
-                    q.o[2] = sh.st.o[2][sidx];
-                    q.u[0] = sh.st.u[0][sidx];
-                    q.u[1] = sh.st.u[1][sidx];
-                    q.u[2] = sh.st.u[2][sidx];
-                    q.w = sh.st.w[sidx];
-                    bnd = push_one<T, SHAPE, NT>(d, sp, s, bx, scx, scy, scz, sF, sh, q,
-                                                 d.pid ? d.pid + idx : nullptr, base + sidx, slot, cb,
-                                                 my_status);
-                    store_part(d, idx, q, false);
-                }
-                const unsigned m = __reduce_max_sync(0xffffffffu, __float_as_uint(bnd));
-                if (lane == 0)
-                    atomicMax(&sh.bound_bits[cb], m);
+            const unsigned stay = __ballot_sync(0xffffffffu, qs[r].cell >= 0);
+            const unsigned m = __reduce_max_sync(0xffffffffu, __float_as_uint(bnd));
+            if (lane == 0) {
+                sh.alive[r * NWARP + wid] = stay;
+                atomicMax(&sh.bound_bits[cb], m);
             }
         }
         __syncthreads();
+        // the particles that stay go back to the list compacted, in chunk
+        // order (the leavers' slots close up; sorted lists stay sorted)
+        {
+            int run = 0, pre[NQ];
+#pragma unroll
+            for (int r = 0; r < NQ; ++r)
+                for (int w = 0; w < NWARP; ++w) {
+                    if (w == wid)
+                        pre[r] = run;
+                    run += __popc(sh.alive[r * NWARP + w]);
+                }
+#pragma unroll
+            for (int r = 0; r < NQ; ++r) {
+                if (qs[r].cell < 0)
+                    continue;
+                const int src = base + r * NT + tid;
+                const int dst = surv + pre[r] + __popc(sh.alive[r * NWARP + wid] & ((1u << lane) - 1u));
+                const bool moved = sort_pass || dst != src;
+                const int64_t idx = gidx(dst);
+                store_part(d, idx, qs[r], moved);
+                if (d.pid && moved)
+                    d.pid[idx] = pids[r];
+            }
+            surv += run;
+        }
         if (tid == 0) {
             sh.ngen[cb ^ 1] = 0;
             sh.bound_bits[cb ^ 1] = 0u;
         }
-        if (DEAL && tid < 32)
+        if (DEAL && T::G == 2 && tid < 32)
             sh.bh[tid] = 0;  // every warp read it before the barrier above; next written after the chunk
         if (!sort_pass && base + C < n)  // the stage is free: the next chunk flies during the deposit
             stage_chunk_async<T, NT>(d, sh, L, base + C, min(C, n - base - C));
@@ -1179,103 +1325,58 @@ __device__ __forceinline__ void push_list(const StepDev& d, const SpeciesDev& sp
             if ((DEAL ? deal_pos<C>(q) : e) < cn && !(sh.rec.l[rslot(e)] >> 24))
                 deposit_common<T, SHAPE, C>(sJi, sh.rec, e, sp.jcoef, scale);
         }
-        // general-window moves: whole groups of 32 lane-parallel, one group
-        // per warp; the rest one move per warp, all lanes on it
+        // general-window moves: set aside for the list's end while they fit
+        // (ngen and ndef are the same in every thread); otherwise whole groups
+        // of 32 lane-parallel, one group per warp, and the rest one move per
+        // warp, all lanes on it
         const int ngen = sh.ngen[cb];
-        const int nfull = ngen & ~31;
-        for (int q = tid; q < nfull; q += NT)
-            deposit_general<T, SHAPE, C>(sJi, sh.rec, sh.rec.gen[q], sp.jcoef, scale);
-        constexpr int NWARP = NT / 32;
-        const int rem = ngen - nfull;
-        for (int t = ((wid - (nfull >> 5)) % NWARP + NWARP) % NWARP; t < rem; t += NWARP)
-            deposit_general_warp<T, SHAPE, C>(sJi, sh.rec, sh.rec.gen[nfull + t], sp.jcoef, scale);
+        if (ndef + ngen <= kGenDefer) {
+            for (int q = tid; q < ngen; q += NT) {
+                const int e = rslot(sh.rec.gen[q]);
+                const int k = ndef + q;
+                const float Dx = sh.rec.D[0][e], Dy = sh.rec.D[1][e], Dz = sh.rec.D[2][e], w = sh.rec.w[e];
+                sh.gd.l[k] = sh.rec.l[e];
+                sh.gd.o[0][k] = sh.rec.o[0][e];
+                sh.gd.o[1][k] = sh.rec.o[1][e];
+                sh.gd.o[2][k] = sh.rec.o[2][e];
+                sh.gd.D[0][k] = Dx;
+                sh.gd.D[1][k] = Dy;
+                sh.gd.D[2][k] = Dz;
+                sh.gd.w[k] = w;
+                atomicMax(&sh.gd_bound_bits, __float_as_uint(move_bound<SHAPE>(sp.jcoef, w, Dx, Dy, Dz)));
+            }
+            ndef += ngen;
+        } else {
+            const int nfull = ngen & ~31;
+            for (int q = tid; q < nfull; q += NT)
+                deposit_general<T, SHAPE, C>(sJi, sh.rec, sh.rec.gen[q], sp.jcoef, scale);
+            const int rem = ngen - nfull;
+            for (int t = ((wid - (nfull >> 5)) % NWARP + NWARP) % NWARP; t < rem; t += NWARP)
+                deposit_general_warp<T, SHAPE, C>(sJi, sh.rec, sh.rec.gen[nfull + t], sp.jcoef, scale);
+        }
         prev_inv = inv;
         if (!sort_pass)
             cp_async_wait_all();
         __syncthreads();
     }
     if (n > 0)
-        fold_tile<N, NT>(sJi, sJf, prev_inv);  // the caller synchronises before the flush
-}
-
-// Fill the holes the leavers left below n - nholes with the survivors above.
-template <class T, int NT>
-__device__ __forceinline__ void compact_list(const StepDev& d, int L, int n, int nh, const int* s_holes,
-                                             int* s_src, int& s_nhead, int& s_nsrc)
-{
-    constexpr int S = T::S;
-    const int tid = threadIdx.x;
-    const int nstay = n - nh;
-    const int* ft = d.ftab + d.foff[L];
-    auto gidx = [&](int slot) -> int64_t { return (int64_t)ft[slot >> d.log2S] * S + (slot & (S - 1)); };
-    auto move_particle = [&](int from, int to) {
-        const int64_t a = gidx(from), b = gidx(to);
-        d.cell[b] = d.cell[a];
-        d.ox[b] = d.ox[a];
-        d.oy[b] = d.oy[a];
-        d.oz[b] = d.oz[a];
-        d.ux[b] = d.ux[a];
-        d.uy[b] = d.uy[a];
-        d.uz[b] = d.uz[a];
-        d.w[b] = d.w[a];
-        if (d.pid)
-            d.pid[b] = d.pid[a];
-    };
-    if (nh <= kHoleCap) {
-        if (tid == 0) {
-            s_nhead = 0;
-            s_nsrc = 0;
+        fold_tile<N, NT>(sJi, sJf, prev_inv);
+    if (ndef > 0) {
+        // the set-aside general-window moves, one per thread, with their own
+        // fixed-point scale (at most kGenDefer terms per node)
+        __syncthreads();
+        float inv;
+        const float scale = chunk_scale(ndef, __uint_as_float(sh.gd_bound_bits), &inv);
+        for (int k = tid; k < ndef; k += NT) {
+            const float o[3] = {sh.gd.o[0][k], sh.gd.o[1][k], sh.gd.o[2][k]};
+            const float D[3] = {sh.gd.D[0][k], sh.gd.D[1][k], sh.gd.D[2][k]};
+            deposit_general_move<T, SHAPE>(sJi, sh.gd.l[k], o, D, sh.gd.w[k], sp.jcoef, scale);
         }
         __syncthreads();
-        // survivors in the tail [nstay, n)
-        for (int t = tid; t < nh; t += NT) {
-            const int slot = nstay + t;
-            if (d.cell[gidx(slot)] != -1)
-                s_src[atomicAdd(&s_nsrc, 1)] = slot;
-        }
-        __syncthreads();
-        // holes in the head [0, nstay): as many as tail survivors
-        for (int t = tid; t < nh; t += NT) {
-            const int hs = s_holes[t];
-            if (hs < nstay)
-                move_particle(s_src[atomicAdd(&s_nhead, 1)], hs);
-        }
-    } else if (tid < 32) {
-        // many leavers: warp-wide two-pointer scan over the list
-        const int lane = tid;
-        int a = 0, b = nstay, ha = 0, hb = 0;
-        unsigned ma = 0, mb = 0;
-        while (true) {
-            while (ma == 0 && a < nstay) {
-                const int slot = a + lane;
-                ma = __ballot_sync(0xffffffffu, slot < nstay && d.cell[gidx(slot)] == -1);
-                ha = a;
-                a += 32;
-            }
-            while (mb == 0 && b < n) {
-                const int slot = b + lane;
-                mb = __ballot_sync(0xffffffffu, slot < n && d.cell[gidx(slot)] != -1);
-                hb = b;
-                b += 32;
-            }
-            if (ma == 0 || mb == 0)
-                break;
-            const int k = min(__popc(ma), __popc(mb));
-            if (lane < k) {  // lane r moves the r-th survivor into the r-th hole
-                unsigned xa = ma, xb = mb;
-                for (int r = 0; r < lane; ++r) {
-                    xa &= xa - 1;
-                    xb &= xb - 1;
-                }
-                move_particle(hb + __ffs(xb) - 1, ha + __ffs(xa) - 1);
-            }
-            __syncwarp();
-            for (int r = 0; r < k; ++r) {
-                ma &= ma - 1;
-                mb &= mb - 1;
-            }
-        }
+        fold_tile<N, NT>(sJi, sJf, inv);
     }
+    // the caller synchronises before the flush
+    return surv;
 }
 
 // ------------------------------------------------------------ the kernel
@@ -1300,9 +1401,11 @@ __global__ void __launch_bounds__(NT, (T::G == 1 ? 1024 : 512) / NT) k_push_depo
 
     // work items: tid 0 asks for the next one while the block works on the
     // current one, and publishes it at the end of the item
-    if (tid == 0)
+    if (tid == 0) {
         sh.item = atomicAdd(d.work_counter, 1);
-    if (tid < 32)
+        sh.nlv = 0;
+    }
+    if (T::G == 2 && tid < 32)
         sh.bh[tid] = 0;  // each chunk clears it after use
     __syncthreads();
     for (;;) {
@@ -1312,6 +1415,9 @@ __global__ void __launch_bounds__(NT, (T::G == 1 ? 1024 : 512) / NT) k_push_depo
         int next_item = 0;
         if (tid == 0)
             next_item = atomicAdd(d.work_counter, 1);
+        // the previous item's leavers into the move buffer (their global
+        // atomics' replies come back while this item starts)
+        flush_leavers<T, NT>(d, sh, my_status);
         const int g = d.items[item];
         const BoxDev bx = d.boxes[d.sc_box[g]];
         const int loc = g - bx.sc_base;
@@ -1327,6 +1433,7 @@ __global__ void __launch_bounds__(NT, (T::G == 1 ? 1024 : 512) / NT) k_push_depo
                     ntot += c;
             }
             sh.any = ntot;
+            sh.nlv = 0;  // every thread read it in flush_leavers (before its barrier, if it had one)
         }
         __syncthreads();
         if (sh.any == 0) {
@@ -1375,9 +1482,9 @@ __global__ void __launch_bounds__(NT, (T::G == 1 ? 1024 : 512) / NT) k_push_depo
             if (!sp.mobile || n == 0)
                 continue;
             if (tid == 0) {
-                sh.nholes = 0;
                 sh.ngen[0] = 0;
                 sh.bound_bits[0] = 0u;
+                sh.gd_bound_bits = 0u;
             }
             if (!sort_pass) {
                 if (s != pre_s)
@@ -1385,20 +1492,16 @@ __global__ void __launch_bounds__(NT, (T::G == 1 ? 1024 : 512) / NT) k_push_depo
                 cp_async_wait_all();
             }
             __syncthreads();
+            int stay;
             if (sp.shape == 2)
-                push_list<T, 2, NT>(d, sp, s, g, bx, scx, scy, scz, sF, sJi, sJf, sh, sort_pass, my_status);
+                stay = push_list<T, 2, NT>(d, sp, s, g, bx, scx, scy, scz, sF, sJi, sJf, sh, sort_pass, my_status);
             else if (T::G == 2 && sp.shape == 3)
-                push_list<T, T::G == 2 ? 3 : 1, NT>(d, sp, s, g, bx, scx, scy, scz, sF, sJi, sJf, sh, sort_pass,
-                                                    my_status);
+                stay = push_list<T, T::G == 2 ? 3 : 1, NT>(d, sp, s, g, bx, scx, scy, scz, sF, sJi, sJf, sh,
+                                                           sort_pass, my_status);
             else
-                push_list<T, 1, NT>(d, sp, s, g, bx, scx, scy, scz, sF, sJi, sJf, sh, sort_pass, my_status);
-            const int nh = sh.nholes;
-            if (nh > 0) {
-                compact_list<T, NT>(d, L, n, nh, sh.holes, sh.src, sh.nhead, sh.nsrc);
-                __syncthreads();
-                if (tid == 0)
-                    d.count[L] = n - nh;
-            }
+                stay = push_list<T, 1, NT>(d, sp, s, g, bx, scx, scy, scz, sF, sJi, sJf, sh, sort_pass, my_status);
+            if (tid == 0 && stay != n)
+                d.count[L] = stay;  // the particles that stay fill the list's first slots
             __syncthreads();
         }
 
@@ -1420,6 +1523,7 @@ __global__ void __launch_bounds__(NT, (T::G == 1 ? 1024 : 512) / NT) k_push_depo
             sh.item = next_item;
         __syncthreads();
     }
+    flush_leavers<T, NT>(d, sh, my_status);
     if (my_status)
         atomicOr(d.status, my_status);
 }

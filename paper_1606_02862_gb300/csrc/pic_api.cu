@@ -18,6 +18,8 @@
 #include <new>
 #include <string>
 #include <vector>
+#include <mutex>
+#include <map>
 
 using namespace pic;
 
@@ -110,6 +112,15 @@ struct pic_ctx {
     float wmax[kMaxSpecies] = {};      // host copy: largest |weight| per species
     int parity = 0;
     bool prepared = false;
+    // subdomain slab (pic_set_subdomain): the two face messages of migrants
+    bool sub_z = false;
+    char* mig = nullptr;
+    int64_t mig_bytes = 0;
+    int mig_cap = 0;
+    int next_stage = 0;  // pic_step_stage: the stage expected next (0 = a step starts)
+    // in-library autotuning (pic_options sc = 0,0,0 and/or threads_per_sc = 0)
+    bool tune_sc = false, tune_threads = false, tune_pending = false;
+    int tune_trials = 0;  // configurations timed by the last tuning (0: given or cached)
     std::vector<int64_t> id_next;  // per (box, species)
     int64_t total_particles = 0;
     // graphs (one per frame-table parity); each holds four event-record
@@ -326,6 +337,10 @@ pic_status status_check(pic_ctx* c)
 
 // ------------------------------------------------------------ mixed form
 
+pic_status insert_mixed(pic_ctx* c, int box, int species, int64_t m, const double* sx, const double* su,
+                        const double* sw, int id_base, const int64_t* ids);
+pic_status autotune(pic_ctx* c);
+
 StepDev make_step(const pic_ctx* c, int parity)
 {
     StepDev d{};
@@ -394,6 +409,9 @@ StepDev make_step(const pic_ctx* c, int parity)
     d.mv_uz = c->mv_uz;
     d.mv_w = c->mv_w;
     d.mv_pid = c->mv_pid;
+    d.mig = c->mig;
+    d.mig_bytes = c->mig_bytes;
+    d.mig_cap = c->mig_cap;
     d.blk_sums = c->blk_sums;
     d.blk_offs = c->blk_offs;
     d.totals = c->totals;
@@ -504,25 +522,51 @@ cudaError_t record(cudaEvent_t e, cudaStream_t s, bool external)
     return external ? cudaEventRecordWithFlags(e, s, cudaEventRecordExternal) : cudaEventRecord(e, s);
 }
 
+YeePlan yee_plan(const pic_ctx* c)
+{
+    return YeePlan{c->boxes_d, c->yee_off_d, c->nboxes, c->yee_nblocks, (float)c->dt,
+                   {(float)(1.0 / c->h[0]), (float)(1.0 / c->h[1]), (float)(1.0 / c->h[2])},
+                   c->step_no, c->dt, {c->h[0], c->h[1], c->h[2]}, c->abs_off_d, c->abs_nblocks,
+                   c->any_antenna ? 1 : 0, c->guard};
+}
+
+// One stage of the mixed-form step (PIC_STAGE_*) on frame-table parity
+// `parity`; the Yee stages run one part of the field update each.
+pic_status enqueue_stage(pic_ctx* c, int stage, int parity)
+{
+    const StepDev d = make_step(c, parity);
+    switch (stage) {
+    case PIC_STAGE_PUSH:
+        CK(cudaMemsetAsync(c->work_counter, 0, sizeof(int), c->stream));
+        CK(cudaMemsetAsync(c->J_all, 0, sizeof(float) * c->field_floats, c->stream));
+        if (c->mig) {  // the face messages start empty (their capacity word stays)
+            CK(cudaMemsetAsync(c->mig, 0, sizeof(int), c->stream));
+            CK(cudaMemsetAsync(c->mig + c->mig_bytes, 0, sizeof(int), c->stream));
+        }
+        CK(launch_push_deposit(d, c->threads, c->push_grid, c->stream));
+        return PIC_OK;
+    case PIC_STAGE_FRAMES:
+        CK(launch_frame_plan(d, c->stream));
+        CK(launch_frame_apply(d, 4 * c->nsm, c->stream));
+        return PIC_OK;
+    default:
+        CK(launch_yee_mixed_part(yee_plan(c), stage - PIC_STAGE_B_FIRST, c->stream));
+        return PIC_OK;
+    }
+}
+
 pic_status enqueue_step_mixed(pic_ctx* c, int parity, cudaEvent_t* ev, bool external = false)
 {
-    StepDev d = make_step(c, parity);
     if (ev)
         CK(record(ev[0], c->stream, external));
-    CK(cudaMemsetAsync(c->work_counter, 0, sizeof(int), c->stream));
-    CK(cudaMemsetAsync(c->J_all, 0, sizeof(float) * c->field_floats, c->stream));
-    CK(launch_push_deposit(d, c->threads, c->push_grid, c->stream));
+    CKS(enqueue_stage(c, PIC_STAGE_PUSH, parity));
     if (ev)
         CK(record(ev[1], c->stream, external));
-    CK(launch_frame_plan(d, c->stream));
-    CK(launch_frame_apply(d, 4 * c->nsm, c->stream));
+    CKS(enqueue_stage(c, PIC_STAGE_FRAMES, parity));
     if (ev)
         CK(record(ev[2], c->stream, external));
-    YeePlan yp{c->boxes_d, c->yee_off_d, c->nboxes, c->yee_nblocks, (float)c->dt,
-               {(float)(1.0 / c->h[0]), (float)(1.0 / c->h[1]), (float)(1.0 / c->h[2])},
-               c->step_no, c->dt, {c->h[0], c->h[1], c->h[2]}, c->abs_off_d, c->abs_nblocks,
-               c->any_antenna ? 1 : 0, c->guard};
-    CK(launch_yee_mixed_plan(yp, c->stream));
+    for (int st = PIC_STAGE_B_FIRST; st <= PIC_STAGE_B_SECOND; ++st)
+        CKS(enqueue_stage(c, st, parity));
     if (ev)
         CK(record(ev[3], c->stream, external));
     return PIC_OK;
@@ -883,7 +927,13 @@ pic_status pic_create(const pic_grid* grids, int32_t nboxes, const double dx[3],
         }
     } else {
         int sc[3] = {o.sc[0], o.sc[1], o.sc[2]};
-        if (sc[0] == 0 && sc[1] == 0 && sc[2] == 0)
+        // zeros: tuned by the library at the first step (tune_candidates);
+        // until then the particles sit in 4 x 4 x 4 supercells / the
+        // supercell's default thread count
+        c->tune_sc = sc[0] == 0 && sc[1] == 0 && sc[2] == 0;
+        c->tune_threads = o.threads_per_sc == 0;
+        c->tune_pending = c->tune_sc || c->tune_threads;
+        if (c->tune_sc)
             sc[0] = sc[1] = sc[2] = 4;
         c->LX = sc[0];
         c->LY = sc[1];
@@ -1003,6 +1053,8 @@ pic_status pic_set_boundary(pic_ctx* c, int32_t box, const pic_boundary* bnd)
         return fail(c, PIC_ERR_ARG, "bad arguments to pic_set_boundary");
     if (c->precision != PIC_PRECISION_MIXED)
         return fail(c, PIC_ERR_ARG, "open y boundaries need the mixed form");
+    if (c->sub_z)
+        return fail(c, PIC_ERR_ARG, "open-y options do not combine with a subdomain slab");
     BoxDev& b = c->boxes_h[box];
     if (bnd->absorber_cells < 0 || 2 * (int64_t)bnd->absorber_cells > b.ny ||
         !(bnd->absorber_sigma >= 0.0) || !std::isfinite(bnd->absorber_sigma))
@@ -1020,6 +1072,8 @@ pic_status pic_set_antenna(pic_ctx* c, int32_t box, const pic_antenna* a)
         return fail(c, PIC_ERR_ARG, "bad arguments to pic_set_antenna");
     if (c->precision != PIC_PRECISION_MIXED)
         return fail(c, PIC_ERR_ARG, "the antenna needs the mixed form");
+    if (c->sub_z)
+        return fail(c, PIC_ERR_ARG, "open-y options do not combine with a subdomain slab");
     BoxDev& b = c->boxes_h[box];
     if (a->plane_y < 0) {
         b.oy.ant_j = -1;
@@ -1052,6 +1106,8 @@ pic_status pic_shift_window(pic_ctx* c, int32_t box, int32_t cells)
         return fail(c, PIC_ERR_ARG, "bad box");
     if (c->precision != PIC_PRECISION_MIXED)
         return fail(c, PIC_ERR_ARG, "the moving window needs the mixed form");
+    if (c->sub_z)
+        return fail(c, PIC_ERR_ARG, "open-y options do not combine with a subdomain slab");
     const BoxDev& b = c->boxes_h[box];
     if (cells <= 0 || cells >= b.ny || cells % c->LY)
         return fail(c, PIC_ERR_ARG, "shift must be a positive multiple of the supercell edge along y, below ny");
@@ -1182,10 +1238,29 @@ pic_status pic_load_particles(pic_ctx* c, int32_t box, int32_t species, int64_t 
             }
             s.n += m;
         } else {
+            CKS(insert_mixed(c, box, species, m, sx, su, sw, (int)(idn + b0), nullptr));
+        }
+    }
+    idn += n;
+    c->total_particles += n;
+    c->prepared = false;
+    return PIC_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Mixed form: convert m particles from device (or mapped host) FP64 arrays
+// into box `box`'s frame lists (ids: per particle, or null for id_base + i).
+pic_status insert_mixed(pic_ctx* c, int box, int species, int64_t m, const double* sx, const double* su,
+                        const double* sw, int id_base, const int64_t* ids)
+{
+    {
+        {
             CKS(ensure_mv(c, std::max<int64_t>(c->mv_cap, m)));
             StepDev d = make_step(c, c->parity);
-            CK(launch_insert_convert(d, box, species, m, sx, su, sw, (int)(idn + b0),
-                                     c->stream));
+            CK(launch_insert_convert(d, box, species, m, sx, su, sw, id_base, ids, c->stream));
             int mi = (int)m;
             CK(cudaMemcpyAsync(c->mv_count, &mi, sizeof(int), cudaMemcpyHostToDevice, c->stream));
             unsigned st = 0;
@@ -1224,11 +1299,12 @@ pic_status pic_load_particles(pic_ctx* c, int32_t box, int32_t species, int64_t 
             c->parity ^= 1;
         }
     }
-    idn += n;
-    c->total_particles += n;
-    c->prepared = false;
     return PIC_OK;
 }
+
+}  // namespace
+
+extern "C" {
 
 pic_status pic_write_fields(pic_ctx* c, int32_t box, int32_t which, const double* f)
 {
@@ -1265,6 +1341,12 @@ pic_status pic_step_async(pic_ctx* c, int32_t nsteps)
         }
         return PIC_OK;
     }
+    if (c->sub_z)
+        return fail(c, PIC_ERR_ARG, "a subdomain context steps through pic_step_stage");
+    if (c->next_stage != PIC_STAGE_PUSH)
+        return fail(c, PIC_ERR_ARG, "a step begun with pic_step_stage is not finished");
+    if (c->tune_pending && nsteps > 0)
+        CKS(autotune(c));
     CKS(prepare_mixed(c));
     if (c->opt.use_graph)
         CKS(capture_graphs(c));
@@ -1316,6 +1398,8 @@ pic_status pic_count_particles(pic_ctx* c, int32_t box, int32_t species, int64_t
     return PIC_OK;
 }
 
+}  // extern "C"
+
 namespace {
 
 // Mixed form: convert the (box, species) particles to FP64 into the device
@@ -1352,7 +1436,265 @@ pic_status read_particles_mixed(pic_ctx* c, int box, int species, double* dx, do
     return PIC_OK;
 }
 
+// ------------------------------------------------------------ in-library autotuning
+
+struct TuneCfg {
+    int sc[3];
+    int threads;
+};
+
+// Supercell shapes and thread counts the push kernel is built for that fit
+// this context: every box a whole number of supercells, the shared memory
+// within the device's limit; only thread counts when the supercell was given.
+std::vector<TuneCfg> tune_candidates(const pic_ctx* c)
+{
+    std::vector<TuneCfg> out;
+    const int edges[2] = {4, 8}, threads[3] = {64, 128, 256};
+    for (int ez : edges)
+        for (int ey : edges)
+            for (int ex : edges)
+                for (int t : threads) {
+                    if (!c->tune_sc && (ex != c->LX || ey != c->LY || ez != c->LZ))
+                        continue;
+                    if (!c->tune_threads && t != c->threads)
+                        continue;
+                    if (!push_supported(ex, ey, ez, t, c->guard) ||
+                        push_smem_bytes(ex, ey, ez, t, c->guard) > c->smem_optin)
+                        continue;
+                    bool fits = true;
+                    for (const pic_grid& g : c->grids)
+                        fits = fits && g.nx % ex == 0 && g.ny % ey == 0 && g.nz % ez == 0;
+                    if (fits)
+                        out.push_back(TuneCfg{{ex, ey, ez}, t});
+                }
+    return out;
+}
+
+// What the result of a tuning depends on: box sizes, species, guard,
+// particles per cell (to 0.5), and which of the two was left to the tuner.
+std::string tune_key(const pic_ctx* c)
+{
+    std::string k;
+    char buf[160];
+    int64_t cells = 0;
+    for (const pic_grid& g : c->grids) {
+        snprintf(buf, sizeof(buf), "%d,%d,%d;", g.nx, g.ny, g.nz);
+        k += buf;
+        cells += (int64_t)g.nx * g.ny * g.nz;
+    }
+    for (const pic_species& p : c->sp) {
+        snprintf(buf, sizeof(buf), "%.17g,%.17g,%d,%d,%d;", p.charge, p.mass, p.shape, p.mobile, p.gather);
+        k += buf;
+    }
+    const double ppc = cells > 0 ? (double)c->total_particles / (double)cells : 0.0;
+    snprintf(buf, sizeof(buf), "g%d|ppc%.1f|%d%d|%d", c->guard, std::round(2.0 * ppc) / 2.0, (int)c->tune_sc,
+             (int)c->tune_threads, c->sort_every);
+    return k + buf;
+}
+
+std::mutex g_tune_mutex;
+std::map<std::string, TuneCfg> g_tune_cache;  // per process
+
+// The particles (FP64 global form, ids when tracked) and the E, B arrays of
+// a context, in device buffers from its allocator.
+struct TuneSnapshot {
+    struct Part {
+        int box, species;
+        int64_t n;
+        double *x, *u, *w;
+        int64_t* id;
+    };
+    std::vector<Part> parts;
+    float *E = nullptr, *B = nullptr;
+};
+
+pic_status take_snapshot(pic_ctx* c, TuneSnapshot* snap)
+{
+    for (int b = 0; b < c->nboxes; ++b)
+        for (int s = 0; s < (int)c->sp.size(); ++s) {
+            int64_t n = 0;
+            CKS(pic_count_particles(c, b, s, &n));
+            TuneSnapshot::Part p{b, s, n, nullptr, nullptr, nullptr, nullptr};
+            if (n > 0) {
+                CKS(dalloc(c, &p.x, 3 * n, false));
+                CKS(dalloc(c, &p.u, 3 * n, false));
+                CKS(dalloc(c, &p.w, n, false));
+                if (c->opt.track_ids)
+                    CKS(dalloc(c, &p.id, n, false));
+                CKS(read_particles_mixed(c, b, s, p.x, p.u, p.w, p.id, nullptr, nullptr, nullptr, nullptr));
+            }
+            snap->parts.push_back(p);
+        }
+    CKS(dalloc(c, &snap->E, c->field_floats, false));
+    CKS(dalloc(c, &snap->B, c->field_floats, false));
+    CK(cudaMemcpyAsync(snap->E, c->E_all, sizeof(float) * c->field_floats, cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemcpyAsync(snap->B, c->B_all, sizeof(float) * c->field_floats, cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return PIC_OK;
+}
+
+void drop_snapshot(pic_ctx* c, TuneSnapshot* snap)
+{
+    for (auto& p : snap->parts) {
+        raw_free(c, p.x);
+        raw_free(c, p.u);
+        raw_free(c, p.w);
+        raw_free(c, p.id);
+    }
+    raw_free(c, snap->E);
+    raw_free(c, snap->B);
+    snap->parts.clear();
+}
+
+// A context like c (grids, cell, time step, species, options, stream,
+// allocator, boundaries, backgrounds, ids) in configuration cfg, holding the
+// snapshot's particles and fields.
+pic_status build_like(pic_ctx* c, const TuneCfg& cfg, const TuneSnapshot& snap, pic_ctx** out)
+{
+    pic_options o = c->opt;
+    o.sc[0] = cfg.sc[0];
+    o.sc[1] = cfg.sc[1];
+    o.sc[2] = cfg.sc[2];
+    o.threads_per_sc = cfg.threads;
+    o.stream = c->stream;
+    pic_ctx* n = nullptr;
+    pic_status st = pic_create(c->grids.data(), c->nboxes, c->h, c->dt, c->sp.data(), (int)c->sp.size(), &o, &n);
+    if (st != PIC_OK)
+        return st;
+    auto bail = [&](pic_status e) {
+        pic_destroy(n);
+        return e;
+    };
+    n->rho_bg = c->rho_bg;
+    for (int b = 0; b < c->nboxes; ++b)
+        n->boxes_h[b].oy = c->boxes_h[b].oy;
+    if ((st = upload_boxes(n)) != PIC_OK)
+        return bail(st);
+    // one pool growth for all insertions: every particle, one part-filled
+    // frame per list, and the first step's headroom
+    int64_t frames = 0;
+    for (const auto& p : snap.parts)
+        frames += (p.n + n->S - 1) / n->S;
+    frames += n->nlists;
+    if ((st = ensure_pool(n, frames + frames / 4 + 1024)) != PIC_OK)
+        return bail(st);
+    for (const auto& p : snap.parts) {
+        if (p.n == 0)
+            continue;
+        if ((st = insert_mixed(n, p.box, p.species, p.n, p.x, p.u, p.w, 0, p.id)) != PIC_OK)
+            return bail(st);
+        n->total_particles += p.n;
+    }
+    n->id_next = c->id_next;
+    if (cudaMemcpyAsync(n->E_all, snap.E, sizeof(float) * c->field_floats, cudaMemcpyDeviceToDevice,
+                        c->stream) != cudaSuccess ||
+        cudaMemcpyAsync(n->B_all, snap.B, sizeof(float) * c->field_floats, cudaMemcpyDeviceToDevice,
+                        c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(PIC_ERR_CUDA);
+    }
+    *out = n;
+    return PIC_OK;
+}
+
+// Push + frame maintenance milliseconds per step of configuration cfg on
+// the snapshot (2 warm-up steps, then 3 timed with the step's stage events).
+double time_config(pic_ctx* c, const TuneCfg& cfg, const TuneSnapshot& snap)
+{
+    pic_ctx* n = nullptr;
+    if (build_like(c, cfg, snap, &n) != PIC_OK)
+        return INFINITY;
+    double ms[4] = {0, 0, 0, 0};
+    int64_t k = 0;
+    const bool ok = pic_step(n, 2) == PIC_OK && pic_stage_timing(n, 1) == PIC_OK && pic_step(n, 3) == PIC_OK &&
+                    pic_stage_times(n, ms, &k) == PIC_OK && k > 0;
+    pic_destroy(n);
+    cudaGetLastError();
+    return ok ? (ms[0] + ms[1]) / (double)k : INFINITY;
+}
+
+// Before the first step of a context created with sc = 0,0,0 and/or
+// threads_per_sc = 0: time every candidate on the loaded state (or take the
+// result of an earlier tuning of the same kind of state in this process),
+// then move the context into the fastest configuration.  The context's
+// state (particles with their ids, fields, backgrounds, boundaries) is the
+// same afterwards; only its supercells and threads change.
+pic_status autotune(pic_ctx* c)
+{
+    c->tune_pending = false;
+    if (c->total_particles == 0 || c->steps_done != 0)
+        return PIC_OK;
+    const std::vector<TuneCfg> cands = tune_candidates(c);
+    if (cands.empty())
+        return PIC_OK;
+    const std::string key = tune_key(c);
+    TuneCfg best = cands[0];
+    bool cached = false;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            best = it->second;
+            cached = true;
+        }
+    }
+    TuneSnapshot snap;
+    pic_status st = take_snapshot(c, &snap);
+    if (st != PIC_OK) {
+        drop_snapshot(c, &snap);
+        return st;
+    }
+    if (!cached) {
+        double best_ms = INFINITY;
+        for (const TuneCfg& cfg : cands) {
+            const double ms = time_config(c, cfg, snap);
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = cfg;
+            }
+        }
+        c->tune_trials = (int)cands.size();
+        if (!(best_ms < INFINITY)) {  // no candidate ran: keep the configuration in use
+            drop_snapshot(c, &snap);
+            return PIC_OK;
+        }
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        g_tune_cache[key] = best;
+    } else {
+        c->tune_trials = 0;
+    }
+    if (best.sc[0] == c->LX && best.sc[1] == c->LY && best.sc[2] == c->LZ && best.threads == c->threads) {
+        drop_snapshot(c, &snap);
+        return PIC_OK;
+    }
+    pic_ctx* n = nullptr;
+    st = build_like(c, best, snap, &n);
+    drop_snapshot(c, &snap);
+    if (st != PIC_OK)
+        return fail(c, st, "autotune: rebuilding the context in supercell %dx%dx%d, %d threads failed",
+                    best.sc[0], best.sc[1], best.sc[2], best.threads);
+    // c takes n's state; n takes c's old state and releases it
+    const bool own = c->own_stream, timing = c->timing;
+    const pic_options user = c->opt;
+    const int trials = c->tune_trials;
+    const int64_t host_direct = c->host_direct;
+    std::swap(*c, *n);
+    c->own_stream = own;
+    n->own_stream = false;
+    c->opt = user;
+    c->tune_trials = trials;
+    c->host_direct = host_direct;
+    c->timing = timing;
+    c->tune_sc = n->tune_sc;
+    c->tune_threads = n->tune_threads;
+    pic_destroy(n);
+    return PIC_OK;
+}
+
 }  // namespace
+
+extern "C" {
 
 pic_status pic_read_particles(pic_ctx* c, int32_t box, int32_t species, int64_t cap, double* x,
                               double* u, double* w, int64_t* id, int64_t* n_out)
@@ -1509,8 +1851,11 @@ pic_status pic_info(pic_ctx* c, int32_t key, int64_t* out)
         return PIC_OK;
     case PIC_INFO_KERNELS_PER_STEP:
         if (c->precision == PIC_PRECISION_MIXED) {
-            // push; scan reduce, top; apply, place, free; Yee x3; antenna; y absorber
-            *out = 1 + 2 + 3 + 3 + (c->any_antenna ? 1 : 0) + (c->abs_nblocks > 0 ? 1 : 0);
+            // push; scan reduce, top; apply, place, free; Yee x3; antenna; y absorber;
+            // a subdomain slab adds its 16 halo pack/unpack launches (J, B, E, B:
+            // two faces each way) and 2 migrant accepts
+            *out = 1 + 2 + 3 + 3 + (c->any_antenna ? 1 : 0) + (c->abs_nblocks > 0 ? 1 : 0) +
+                   (c->sub_z ? 18 : 0);
         } else {
             int64_t k = 0;
             for (int b = 0; b < c->nboxes; ++b) {
@@ -1543,9 +1888,193 @@ pic_status pic_info(pic_ctx* c, int32_t key, int64_t* out)
     case PIC_INFO_MOVE_CAPACITY:
         *out = c->mv_cap;
         return PIC_OK;
+    case PIC_INFO_SUPERCELL_X:
+    case PIC_INFO_SUPERCELL_Y:
+    case PIC_INFO_SUPERCELL_Z:
+        *out = c->precision == PIC_PRECISION_MIXED
+                   ? (key == PIC_INFO_SUPERCELL_X ? c->LX : (key == PIC_INFO_SUPERCELL_Y ? c->LY : c->LZ))
+                   : 0;
+        return PIC_OK;
+    case PIC_INFO_THREADS:
+        *out = c->precision == PIC_PRECISION_MIXED ? c->threads : 0;
+        return PIC_OK;
+    case PIC_INFO_TUNE_TRIALS:
+        *out = c->tune_trials;
+        return PIC_OK;
     default:
         return fail(c, PIC_ERR_ARG, "unknown info key %d", key);
     }
+}
+
+// ------------------------------------------------------------ domain decomposition (z slabs)
+
+pic_status pic_set_subdomain(pic_ctx* c, int32_t box, const pic_subdomain* sub)
+{
+    CKS(check_ctx(c));
+    if (!sub || box != 0 || c->nboxes != 1)
+        return fail(c, PIC_ERR_ARG, "a subdomain is box 0 of a one-box context");
+    if (c->precision != PIC_PRECISION_MIXED)
+        return fail(c, PIC_ERR_ARG, "subdomains need the mixed form");
+    if (c->next_stage != PIC_STAGE_PUSH)
+        return fail(c, PIC_ERR_ARG, "pic_set_subdomain in the middle of a step");
+    BoxDev& b = c->boxes_h[0];
+    if (b.oy.open_y || b.oy.abs_cells > 0 || b.oy.ant_j >= 0)
+        return fail(c, PIC_ERR_ARG, "open-y options do not combine with a subdomain slab");
+    if (sub->migrant_capacity < 0 || sub->migrant_capacity > (1 << 26))
+        return fail(c, PIC_ERR_ARG, "migrant_capacity out of range");
+    if (sub->id_base < 0 || sub->id_base > INT32_MAX)
+        return fail(c, PIC_ERR_ARG, "id_base out of range");
+    if (sub->enable) {
+        const int64_t cap = sub->migrant_capacity > 0 ? sub->migrant_capacity : 2 * (int64_t)b.nx * b.ny;
+        if (cap != c->mig_cap) {
+            CK(cudaStreamSynchronize(c->stream));
+            raw_free(c, c->mig);
+            c->mig = nullptr;
+            const int64_t bytes = (int64_t)sizeof(MigHeader) + cap * (int64_t)sizeof(MigRec);
+            CKS(dalloc(c, &c->mig, 2 * bytes, true));
+            const MigHeader h{0, (int)cap, {0, 0}};
+            CK(cudaMemcpyAsync(c->mig, &h, sizeof(h), cudaMemcpyHostToDevice, c->stream));
+            CK(cudaMemcpyAsync(c->mig + bytes, &h, sizeof(h), cudaMemcpyHostToDevice, c->stream));
+            c->mig_bytes = bytes;
+            c->mig_cap = (int)cap;
+        }
+    }
+    b.sub_z = sub->enable ? 1 : 0;
+    c->sub_z = sub->enable != 0;
+    if (c->sub_z)
+        c->tune_pending = false;  // slabs keep the configuration they were created with
+    if (sub->enable)
+        for (auto& v : c->id_next)
+            v = sub->id_base;
+    destroy_graphs(c);
+    return upload_boxes(c);
+}
+
+pic_status pic_step_stage(pic_ctx* c, int32_t stage)
+{
+    CKS(check_ctx(c));
+    if (c->precision != PIC_PRECISION_MIXED)
+        return fail(c, PIC_ERR_ARG, "pic_step_stage needs the mixed form");
+    if (stage != c->next_stage)
+        return fail(c, PIC_ERR_ARG, "stage %d out of order (expected %d)", stage, c->next_stage);
+    if (stage == PIC_STAGE_PUSH)
+        CKS(prepare_mixed(c));
+    CKS(enqueue_stage(c, stage, c->parity));
+    if (stage == PIC_STAGE_FRAMES) {
+        c->parity ^= 1;
+        ++c->steps_done;
+    }
+    c->next_stage = (stage + 1) % (PIC_STAGE_B_SECOND + 1);
+    return PIC_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Padded z planes [p0, p0 + np) of a subdomain box's halo message or its
+// target: pack = the message to the neighbour on `side`, else the planes the
+// message from the neighbour on `side` goes into.  E, B: interior planes the
+// neighbour keeps as guards / this slab's guards; J: this slab's guards /
+// its interior planes on that face.
+void halo_planes(const BoxDev& b, int which, int side, bool pack, int* p0, int* np)
+{
+    const int G = b.gz, top = b.pz - b.gz - b.nz;  // guard planes below / above
+    const bool j = which == PIC_FIELD_J;
+    if (j == pack) {  // E/B unpack or J pack: the guard planes of that face
+        *p0 = side == 0 ? 0 : G + b.nz;
+        *np = side == 0 ? G : top;
+    } else {          // E/B pack or J unpack: the interior planes of that face
+        *p0 = side == 0 ? G : b.nz;
+        *np = side == 0 ? top : G;
+    }
+}
+
+pic_status halo_check(pic_ctx* c, int box, int which, int side)
+{
+    CKS(check_ctx(c));
+    if (!c->sub_z || box != 0)
+        return fail(c, PIC_ERR_ARG, "halos belong to a subdomain box (pic_set_subdomain)");
+    if ((which != PIC_FIELD_E && which != PIC_FIELD_B && which != PIC_FIELD_J) || (side != 0 && side != 1))
+        return fail(c, PIC_ERR_ARG, "bad field or side");
+    return PIC_OK;
+}
+
+float* field_of(pic_ctx* c, int which)
+{
+    const BoxDev& b = c->boxes_h[0];
+    return which == PIC_FIELD_E ? b.E : (which == PIC_FIELD_B ? b.B : b.J);
+}
+
+}  // namespace
+
+extern "C" {
+
+pic_status pic_halo_floats(pic_ctx* c, int32_t box, int32_t which, int32_t side, int64_t* nfloats)
+{
+    CKS(halo_check(c, box, which, side));
+    if (!nfloats)
+        return fail(c, PIC_ERR_ARG, "nfloats is NULL");
+    int p0 = 0, np = 0;
+    const BoxDev& b = c->boxes_h[0];
+    halo_planes(b, which, side, true, &p0, &np);
+    *nfloats = 3 * (int64_t)b.px * b.py * np;
+    return PIC_OK;
+}
+
+pic_status pic_halo_pack(pic_ctx* c, int32_t box, int32_t which, int32_t side, float* buf)
+{
+    CKS(halo_check(c, box, which, side));
+    if (!buf)
+        return fail(c, PIC_ERR_ARG, "buf is NULL");
+    int p0 = 0, np = 0;
+    const BoxDev& b = c->boxes_h[0];
+    halo_planes(b, which, side, true, &p0, &np);
+    CK(launch_halo_planes(b, field_of(c, which), p0, np, buf, 0, c->stream));
+    return PIC_OK;
+}
+
+pic_status pic_halo_unpack(pic_ctx* c, int32_t box, int32_t which, int32_t side, const float* buf)
+{
+    CKS(halo_check(c, box, which, side));
+    if (!buf)
+        return fail(c, PIC_ERR_ARG, "buf is NULL");
+    int p0 = 0, np = 0;
+    const BoxDev& b = c->boxes_h[0];
+    halo_planes(b, which, side, false, &p0, &np);
+    CK(launch_halo_planes(b, field_of(c, which), p0, np, const_cast<float*>(buf),
+                          which == PIC_FIELD_J ? 2 : 1, c->stream));
+    return PIC_OK;
+}
+
+pic_status pic_migrant_bytes(pic_ctx* c, int64_t* bytes)
+{
+    CKS(check_ctx(c));
+    if (!c->sub_z || !bytes)
+        return fail(c, PIC_ERR_ARG, "migrant messages belong to a subdomain context");
+    *bytes = c->mig_bytes;
+    return PIC_OK;
+}
+
+pic_status pic_migrants_pack(pic_ctx* c, int32_t side, void* buf)
+{
+    CKS(check_ctx(c));
+    if (!c->sub_z || (side != 0 && side != 1) || !buf)
+        return fail(c, PIC_ERR_ARG, "bad arguments to pic_migrants_pack");
+    CK(cudaMemcpyAsync(buf, c->mig + side * c->mig_bytes, (size_t)c->mig_bytes, cudaMemcpyDeviceToDevice,
+                       c->stream));
+    return PIC_OK;
+}
+
+pic_status pic_migrants_accept(pic_ctx* c, int32_t side, const void* buf)
+{
+    CKS(check_ctx(c));
+    if (!c->sub_z || (side != 0 && side != 1) || !buf)
+        return fail(c, PIC_ERR_ARG, "bad arguments to pic_migrants_accept");
+    if (c->next_stage != PIC_STAGE_FRAMES)
+        return fail(c, PIC_ERR_ARG, "migrants are accepted between the PUSH and FRAMES stages");
+    CK(launch_mig_accept(make_step(c, c->parity), 0, side, static_cast<const char*>(buf), c->stream));
+    return PIC_OK;
 }
 
 const char* pic_last_error(const pic_ctx* c)

@@ -12,6 +12,10 @@
 //   deposits that the Yee E update folds back into the periodic images.  The
 //   padding lets every supercell read its E/B tile and write its J tile as one
 //   regular box, 16-byte aligned along x (supercell edges are multiples of 4).
+//   A box that is one z slab of a decomposed box (sub_z) keeps x and y
+//   periodic; its z guards are exchanged with the neighbouring slabs instead
+//   (E, B: copies of the neighbour's interior; J: sent to the neighbour and
+//   added there), and particles leaving through a z face are sent on.
 //
 //   Particles live in frames (Sec. 2.1): a frame has S slots, S = cells per
 //   supercell; attribute arrays are indexed frame * S + slot.  Each (species,
@@ -71,6 +75,7 @@ struct BoxDev {
     int gx, gy, gz;           // guard cells below the interior (above: p - n - g)
     int nscx, nscy, nscz;     // supercells per axis
     int sc_base;              // first global supercell id of the box
+    int sub_z;                // one z slab of a decomposed box: z faces exchange, no z wrap
     float* E;                 // 3 * px*py*pz, component-major
     float* B;
     float* J;
@@ -127,6 +132,12 @@ struct StepDev {
     float* mv_uz;
     float* mv_w;
     int* mv_pid;
+    // particles leaving a subdomain box through a z face this step: one
+    // message per face (MigHeader + mig_cap MigRec records), face f at
+    // mig + f * mig_bytes
+    char* mig;
+    int64_t mig_bytes;
+    int mig_cap;
     // scan scratch
     int4* blk_sums;           // [scan blocks]
     int4* blk_offs;           // [scan blocks]
@@ -138,6 +149,21 @@ struct StepDev {
     unsigned* status;         // device status word
     unsigned* wmax_bits;      // [kMaxSpecies] float bits of the largest |weight| loaded
 };
+
+// A particle that left a subdomain box through a z face (48 bytes): the
+// neighbour puts it into supercell (sx, sy, its row on that face).
+struct MigRec {
+    int s, sx, sy, cell;
+    float ox, oy, oz, ux;
+    float uy, uz, w;
+    int pid;
+};
+struct MigHeader {
+    int count;  // particles written (may exceed cap: the rest were dropped)
+    int cap;
+    int pad[2];
+};
+static_assert(sizeof(MigRec) == 48 && sizeof(MigHeader) == 16, "migrant message layout");
 
 // ---------------------------------------------------------------- helpers
 
@@ -177,13 +203,21 @@ size_t push_smem_bytes(int LX, int LY, int LZ, int threads, int guard);
 int frame_scan_blocks(int nlists);
 cudaError_t launch_frame_plan(const StepDev& d, cudaStream_t st);
 cudaError_t launch_frame_apply(const StepDev& d, int place_blocks, cudaStream_t st);
+// ids: per-particle ids (or null: id_base + i)
 cudaError_t launch_insert_convert(const StepDev& d, int box, int species, int64_t n,
                                   const double* x, const double* u, const double* w,
-                                  int id_base, cudaStream_t st);
+                                  int id_base, const int64_t* ids, cudaStream_t st);
 cudaError_t launch_read_particles(const StepDev& d, const BoxDev& hb, int box, int species,
                                   const int* list_off, double* x, double* u, double* w,
                                   int64_t* id, cudaStream_t st);
 cudaError_t launch_yee_mixed_plan(const YeePlan& p, cudaStream_t st);
+// one part of the field update: 0 = B half, 1 = antenna + E, 2 = B half + absorber
+cudaError_t launch_yee_mixed_part(const YeePlan& p, int part, cudaStream_t st);
+// planes [p0, p0 + np) (padded z) of the 3 components of F <-> buf
+// ([comp][plane][py][px]); mode 0: F -> buf, 1: buf -> F, 2: F += buf
+cudaError_t launch_halo_planes(const BoxDev& b, float* F, int p0, int np, float* buf, int mode,
+                               cudaStream_t st);
+cudaError_t launch_mig_accept(const StepDev& d, int box, int side, const char* msg, cudaStream_t st);
 int absorber_blocks(const BoxDev& b);
 cudaError_t launch_shift_fields(const BoxDev& b, float* F, const float* scratch, int cells,
                                 cudaStream_t st);

@@ -33,9 +33,13 @@ EXPORTED = ("pic_create", "pic_set_background", "pic_set_boundary", "pic_set_ant
             "pic_shift_window", "pic_load_particles", "pic_write_fields",
             "pic_step", "pic_step_async", "pic_sync", "pic_read_fields", "pic_count_particles",
             "pic_read_particles", "pic_diagnostics", "pic_stage_timing", "pic_stage_times",
-            "pic_info", "pic_field_energy_noalloc", "pic_last_error", "pic_destroy")
+            "pic_info", "pic_set_subdomain", "pic_step_stage", "pic_halo_floats", "pic_halo_pack",
+            "pic_halo_unpack", "pic_migrant_bytes", "pic_migrants_pack", "pic_migrants_accept",
+            "pic_field_energy_noalloc", "pic_last_error", "pic_destroy")
+STAGE_PUSH, STAGE_FRAMES, STAGE_B_FIRST, STAGE_E, STAGE_B_SECOND = range(5)
 (INFO_GRAPH_ACTIVE, INFO_KERNELS_PER_STEP, INFO_POOL_FRAMES, INFO_FRAMES_USED, INFO_MOVE_CAPACITY,
- INFO_STEPS, INFO_HOST_DIRECT) = range(7)
+ INFO_STEPS, INFO_HOST_DIRECT, INFO_SUPERCELL_X, INFO_SUPERCELL_Y, INFO_SUPERCELL_Z, INFO_THREADS,
+ INFO_TUNE_TRIALS) = range(12)
 
 
 class PicError(RuntimeError):
@@ -65,6 +69,11 @@ class Boundary(ctypes.Structure):
 class AntennaC(ctypes.Structure):
     _fields_ = [("plane_y", ctypes.c_int32), ("reserved", ctypes.c_int32)] + \
         [(k, ctypes.c_double) for k in ("E0", "omega", "w0", "xc", "zc", "tau", "t0")]
+
+
+class Subdomain(ctypes.Structure):
+    _fields_ = [("enable", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("migrant_capacity", ctypes.c_int64), ("id_base", ctypes.c_int64)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
@@ -112,6 +121,14 @@ def library(path: str = LIB_PATH):
     L.pic_stage_timing.argtypes = [vp, i32]
     L.pic_stage_times.argtypes = [vp, dp, ctypes.POINTER(i64)]
     L.pic_info.argtypes = [vp, i32, ctypes.POINTER(i64)]
+    L.pic_set_subdomain.argtypes = [vp, i32, ctypes.POINTER(Subdomain)]
+    L.pic_step_stage.argtypes = [vp, i32]
+    L.pic_halo_floats.argtypes = [vp, i32, i32, i32, ctypes.POINTER(i64)]
+    L.pic_halo_pack.argtypes = [vp, i32, i32, i32, vp]
+    L.pic_halo_unpack.argtypes = [vp, i32, i32, i32, vp]
+    L.pic_migrant_bytes.argtypes = [vp, ctypes.POINTER(i64)]
+    L.pic_migrants_pack.argtypes = [vp, i32, vp]
+    L.pic_migrants_accept.argtypes = [vp, i32, vp]
     L.pic_field_energy_noalloc.argtypes = [vp, vp, i64, ctypes.c_double, vp, vp]
     L.pic_last_error.argtypes = [vp]
     L.pic_last_error.restype = ctypes.c_char_p
@@ -175,8 +192,15 @@ class Context:
     """One libpic context: nboxes periodic boxes sharing dx, dt and species."""
 
     def __init__(self, grids, dx, dt, species, precision=PRECISION_MIXED, sc=(4, 4, 4),
-                 threads_per_sc=0, track_ids=False, use_graph=True, pool_frames=0,
+                 threads_per_sc=None, track_ids=False, use_graph=True, pool_frames=0,
                  move_capacity=0, torch_memory=True, sort_every=0):
+        """sc = (0, 0, 0) and/or threads_per_sc = 0 leave the configuration
+        to the library's tuner (at the first step); threads_per_sc = None
+        takes the supercell's default (256 threads from 256 cells on, else
+        128)."""
+        if threads_per_sc is None:
+            cells = int(sc[0]) * int(sc[1]) * int(sc[2])
+            threads_per_sc = 256 if cells >= 256 else 128
         L = library()
         self._L = L
         self._ctx = ctypes.c_void_p()
@@ -244,6 +268,11 @@ class Context:
 
     def steps_taken(self):
         return self.info(INFO_STEPS)
+
+    def config(self):
+        """(supercell edges, threads per supercell) in use (mixed form)."""
+        return ((self.info(INFO_SUPERCELL_X), self.info(INFO_SUPERCELL_Y), self.info(INFO_SUPERCELL_Z)),
+                self.info(INFO_THREADS))
 
     def load_particles(self, box, species, x, u, w=None):
         x = _f64(x, (-1, 3))
@@ -333,6 +362,37 @@ class Context:
         self._check(self._L.pic_info(self._ctx, int(key), ctypes.byref(v)))
         return v.value
 
+    # ------------------------------------------------------------ z-slab subdomains
+    def set_subdomain(self, enable=True, migrant_capacity=0, id_base=0):
+        """Make box 0 one z slab of a decomposed box (pic_set_subdomain)."""
+        sd = Subdomain(int(bool(enable)), 0, int(migrant_capacity), int(id_base))
+        self._check(self._L.pic_set_subdomain(self._ctx, 0, ctypes.byref(sd)))
+
+    def step_stage(self, stage):
+        self._check(self._L.pic_step_stage(self._ctx, int(stage)))
+
+    def halo_floats(self, which, side):
+        n = ctypes.c_int64()
+        self._check(self._L.pic_halo_floats(self._ctx, 0, int(which), int(side), ctypes.byref(n)))
+        return n.value
+
+    def halo_pack(self, which, side, buf_ptr):
+        self._check(self._L.pic_halo_pack(self._ctx, 0, int(which), int(side), ctypes.c_void_p(buf_ptr)))
+
+    def halo_unpack(self, which, side, buf_ptr):
+        self._check(self._L.pic_halo_unpack(self._ctx, 0, int(which), int(side), ctypes.c_void_p(buf_ptr)))
+
+    def migrant_bytes(self):
+        n = ctypes.c_int64()
+        self._check(self._L.pic_migrant_bytes(self._ctx, ctypes.byref(n)))
+        return n.value
+
+    def migrants_pack(self, side, buf_ptr):
+        self._check(self._L.pic_migrants_pack(self._ctx, int(side), ctypes.c_void_p(buf_ptr)))
+
+    def migrants_accept(self, side, buf_ptr):
+        self._check(self._L.pic_migrants_accept(self._ctx, int(side), ctypes.c_void_p(buf_ptr)))
+
     def last_error(self):
         msg = self._L.pic_last_error(self._ctx)
         return msg.decode() if msg else ""
@@ -366,7 +426,7 @@ def field_energy_noalloc(E_ptr, B_ptr, ncells, cell_volume, out_ptr, stream=None
         raise PicError(st, "pic_field_energy_noalloc failed")
 
 
-def from_workload(wl, precision=PRECISION_MIXED, sc=(4, 4, 4), threads_per_sc=0, track_ids=False,
+def from_workload(wl, precision=PRECISION_MIXED, sc=(4, 4, 4), threads_per_sc=None, track_ids=False,
                   use_graph=True, **kw) -> Context:
     """Create a context for a workloads.Workload and load its initial state."""
     ctx = Context([(b.nx, b.ny, b.nz) for b in wl.boxes], wl.dx, wl.dt,

@@ -170,16 +170,21 @@ def thermal_tsc(n=256, ppc=8, u_th=0.05, seed_offset=1, ny=None, nz=None) -> Wor
                     steps=200)
 
 
-def fill_thermal(x, u, w, nx, ny, nz, ppc, u_th, dens=0.01, seed_offset=1, slab=8):
+def fill_thermal(x, u, w, nx, ny, nz, ppc, u_th, dens=0.01, seed_offset=1, slab=8, z_lo=0, z_hi=None):
     """Write the thermal_tsc recipe (ppc uniform positions per cell,
     Maxwellian u_th, weight dens / ppc) into preallocated (n,3), (n,3), (n,)
     float64 arrays, one z-slab at a time with its own PCG64 stream, so that a
     256^3 state (134M particles) never needs more than the output arrays.
-    Returns the particle count written."""
+    z_lo, z_hi (multiples of `slab`): only the planes [z_lo, z_hi), the same
+    particles as that part of the whole box.  Returns the particle count
+    written."""
     per_layer = nx * ny * ppc
+    z_hi = nz if z_hi is None else z_hi
+    if z_lo % slab or (z_hi % slab and z_hi != nz) or not 0 <= z_lo <= z_hi <= nz:
+        raise ValueError("z range must be whole generator slabs")
     k = 0
-    for z0 in range(0, nz, slab):
-        z1 = min(nz, z0 + slab)
+    for z0 in range(z_lo, z_hi, slab):
+        z1 = min(z_hi, z0 + slab)
         rng = np.random.default_rng([BASE_SEED + seed_offset, z0])
         cz, cy, cx = np.meshgrid(np.arange(z0, z1), np.arange(ny), np.arange(nx), indexing="ij")
         m = (z1 - z0) * per_layer
