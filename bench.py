@@ -43,7 +43,8 @@ MIXED_BYTES_PER_CELL = 36.0
 PLAIN_BYTES_PER_PARTICLE = 104.0
 PLAIN_BYTES_PER_CELL = 72.0
 PUSH_KERNEL_SRC = os.path.join(ROOT, "paper_1606_02862_gb300", "csrc", "k_push.cu")
-TRAFFIC_SUMMARY = os.path.join(ROOT, "profiles", "push_deposit_thermal_tsc.md")
+# machine-readable figures of the committed ncu summary of the push kernel
+TRAFFIC_SUMMARY = os.path.join(ROOT, "profiles", "push_deposit_thermal_tsc.json")
 
 
 def log(*a):
@@ -62,28 +63,23 @@ def measured_hbm():
 
 def push_profile():
     """Per-particle DRAM bytes, L1 data-pipe wavefronts (shared memory and
-    global LSU traffic; shared only when the summary lacks them) and FP32
-    operations of the push kernel from the committed ncu summary (thermal
-    TSC, 8x4x4 supercells, 256 threads), or Nones when the summary is absent
-    or the kernel source changed since the counters were taken."""
+    global LSU traffic) and FP32 operations of the push kernel from the
+    committed ncu figures (thermal TSC, 8x4x4 supercells, 256 threads, a
+    JSON file beside the summary), or Nones when the file is absent or the
+    kernel source changed since the counters were taken."""
     none = {"tpp": None, "wpp": None, "fpp": None, "wkind": None}
     try:
         with open(PUSH_KERNEL_SRC, "rb") as f:
             sha = hashlib.sha256(f.read()).hexdigest()
-        vals = {}
         with open(TRAFFIC_SUMMARY) as f:
-            for line in f:
-                if ":" in line and line.strip().startswith("- "):
-                    k, v = line.strip()[2:].split(":", 1)
-                    vals[k.strip()] = v.strip().strip("`")
-        if vals.get("k_push.cu sha256") != sha:
+            prof = json.load(f)
+        if prof.get("kernel_source_sha256") != sha:
             return none
-        lsu = "l1 data-pipe wavefronts per particle"
-        return {"tpp": float(vals["dram bytes per particle"]),
-                "wpp": float(vals[lsu] if lsu in vals else vals["shared wavefronts per particle"]),
-                "wkind": "l1" if lsu in vals else "smem",
-                "fpp": float(vals["fp32 operations per particle"]) if "fp32 operations per particle" in vals
-                else None}
+        l1 = prof.get("l1_wavefronts_per_particle")
+        return {"tpp": float(prof["dram_bytes_per_particle"]),
+                "wpp": float(l1 if l1 is not None else prof["shared_wavefronts_per_particle"]),
+                "wkind": "l1" if l1 is not None else "smem",
+                "fpp": float(prof["fp32_ops_per_particle"]) if "fp32_ops_per_particle" in prof else None}
     except Exception:  # noqa: BLE001
         return none
 
@@ -234,45 +230,43 @@ def cpu_baseline_oracle(steps=15, n=32, ppc=8):
     return {"value": x.shape[0] * steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"thermal_tsc recipe on a {n}^3 box ({x.shape[0]} particles, TSC, 8 ppc), "
                       f"{steps} full steps, single-threaded FP64 C oracle ({dt:.1f} s)",
-            "cpu": cpu_model()}
+            "cpu": cpu_model(), "threads_used": 1}
+
+
+# Arm CPU part numbers (/proc/cpuinfo "CPU part") of the hosts this may run on
+ARM_PARTS = {"0xd4f": "Arm Neoverse-V2", "0xd40": "Arm Neoverse-V1", "0xd0c": "Arm Neoverse-N1",
+             "0xd49": "Arm Neoverse-N2", "0xd84": "Arm Neoverse-V3"}
 
 
 def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo; Arm part numbers
+    are named), its architecture, and the cores this process may run on."""
+    name = None
     try:
-        with open("/proc/cpuinfo") as f:
-            for line in f:
-                if line.lower().startswith(("model name", "cpu part", "hardware")):
-                    return line.split(":", 1)[1].strip()
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                name = line.split(":", 1)[1].strip()
+                break
     except Exception:  # noqa: BLE001
         pass
-    return os.uname().machine
-
-
-def choose_sc(args, pic, log_fn):
-    """Supercell and threads: from --sc/--threads, or (--sc auto) the autotuner
-    run on a 64^3 sample of the same recipe, cached per GPU and build."""
-    from paper_1606_02862_gb300 import autotune
-    from paper_1606_02862_gb300 import workloads as W
-
-    if args.sc != "auto":
-        return tuple(int(v) for v in args.sc.split("x")), args.threads
-    import torch
-
-    n, ppc = 64, 8
-    X, U, Wt = make_state(torch, n, ppc, 0.05, pinned=False)
-
-    def make_ctx(sc, threads):
-        ctx = pic.Context([(n, n, n)], (1.0, 1.0, 1.0), W.DT_HALF_COURANT,
-                          [pic.Species(-1.0, 1.0, SHAPE[args.shape])], sc=sc, threads_per_sc=threads)
-        ctx.set_background(0, 0.01)
-        load(ctx, X, U, Wt)
-        return ctx
-
-    key = autotune.signature([(args.n,) * 3], ppc, [SHAPE[args.shape]], 1, extra="thermal")
-    sc, threads, trials = autotune.tune(make_ctx, autotune.feasible(autotune.CANDIDATES, [(n, n, n)]),
-                                        key=key, gpu_name=torch.cuda.get_device_name(), log=log_fn)
-    log_fn(f"autotune: supercell {sc}, {threads} threads ({len(trials)} timed, cached otherwise)")
-    return sc, threads
+    if not name:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for line in f:
+                    key = line.split(":", 1)[0].strip().lower()
+                    if key in ("model name", "cpu part", "hardware"):
+                        v = line.split(":", 1)[1].strip()
+                        name = ARM_PARTS.get(v, v)
+                        break
+        except Exception:  # noqa: BLE001
+            pass
+    try:
+        usable = len(os.sched_getaffinity(0))
+    except Exception:  # noqa: BLE001
+        usable = os.cpu_count()
+    return {"model": name or os.uname().machine, "arch": os.uname().machine, "nproc": usable,
+            "logical_cpus": os.cpu_count()}
 
 
 def run_batched(args, pic, torch, sc, threads, hbm, rank=0, world=1, dist=None):
@@ -296,6 +290,8 @@ def run_batched(args, pic, torch, sc, threads, hbm, rank=0, world=1, dist=None):
     npart, ncell = int(npart), int(ncell)
     out = {"workload": f"batched_uneven: {len(boxes)} periodic boxes, edges 16..96, ppc 1..16, "
                        f"u_th 0.01..0.1c, TSC ({npart} particles, {ncell} cells)"}
+    if getattr(args, "auto", False):
+        sc, threads = (0, 0, 0), 0  # libpic tunes on this state at its first step
     for prec, steps, name in ((pic.PRECISION_MIXED, max(10, args.steps // 5), "mixed"),
                               (pic.PRECISION_FP64_PLAIN, 2, "plain_fp64")):
         if prec == pic.PRECISION_FP64_PLAIN and args.no_plain:
@@ -306,6 +302,7 @@ def run_batched(args, pic, torch, sc, threads, hbm, rank=0, world=1, dist=None):
             ctx.set_background(bi, 0.01)
             ctx.load_particles(bi, 0, x, u, w)
         ctx.step(3 if prec == pic.PRECISION_MIXED else 1)
+        cfg = ctx.config() if prec == pic.PRECISION_MIXED else None
         ctx.stage_timing(True)
         ctx.step(steps)
         ms, nst = ctx.stage_times()
@@ -315,6 +312,7 @@ def run_batched(args, pic, torch, sc, threads, hbm, rank=0, world=1, dist=None):
         per_p = MIXED_BYTES_PER_PARTICLE if prec == pic.PRECISION_MIXED else PLAIN_BYTES_PER_PARTICLE
         per_c = MIXED_BYTES_PER_CELL if prec == pic.PRECISION_MIXED else PLAIN_BYTES_PER_CELL
         out[name] = {"value": npart / (pd * 1e-3), "unit": UNIT, "push_deposit_ms": pd,
+                     **({"supercell": "x".join(map(str, cfg[0])), "threads": cfg[1]} if cfg else {}),
                      "step_ms": step_ms, "steps": nst,
                      "hbm_frac": (npart * per_p + ncell * per_c) / world / (push_ms * 1e-3) / 1e9 / hbm}
         log(f"[rank {rank}] batched {name}: push+deposit {pd:.3f} ms, step {step_ms:.3f} ms")
@@ -341,9 +339,10 @@ def run_ours(args, rank, world, dist):
     torch.cuda.set_stream(stream)
 
     n, ppc, u_th = args.n, 8, 0.05
-    sc, threads = choose_sc(args, pic, log)
-    args.threads = threads
-    args.sc = "x".join(str(v) for v in sc)
+    # --sc auto: zeros, so that libpic tunes supercell and threads on the
+    # loaded state at the first (warm-up) step
+    args.auto = args.sc == "auto"
+    sc, threads = ((0, 0, 0), 0) if args.auto else (tuple(int(v) for v in args.sc.split("x")), args.threads)
     ncell = n ** 3
     t0 = time.perf_counter()
     X, U, Wt = make_state(torch, n, ppc, u_th)
@@ -354,11 +353,18 @@ def run_ours(args, rank, world, dist):
     result = {}
 
     # ---------------- mixed form, device-resident inputs, graph replay
-    ctx = new_ctx(pic, n, pic.PRECISION_MIXED, sc, args.threads, SHAPE[args.shape], GATHER[args.gather])
+    ctx = new_ctx(pic, n, pic.PRECISION_MIXED, sc, threads, SHAPE[args.shape], GATHER[args.gather])
     t0 = time.perf_counter()
     load(ctx, X, U, Wt)
     log(f"[rank {rank}] loaded in {time.perf_counter() - t0:.1f} s")
+    t0 = time.perf_counter()
     ctx.step(args.warmup)
+    sc, threads = ctx.config()
+    tune_trials = ctx.info(pic.INFO_TUNE_TRIALS)
+    args.threads = threads
+    args.sc = "x".join(str(v) for v in sc)
+    log(f"[rank {rank}] supercell {args.sc}, {threads} threads ({tune_trials} configurations timed by "
+        f"libpic's tuner); warm-up {time.perf_counter() - t0:.1f} s")
     ctx.stage_timing(True)
     torch.cuda.synchronize()
     if dist is not None:
@@ -466,7 +472,8 @@ def run_ours(args, rank, world, dist):
         "data": "synthetic",
         "config": {"workload": thermal_workload_name(args, n, ppc),
                    "form": f"mixed: int32 cell + FP32 offsets, supercell frames {args.sc}, "
-                           f"{args.threads or 'default'} threads/supercell",
+                           f"{args.threads} threads/supercell"
+                           + (f" (tuned by libpic over {tune_trials} configurations)" if tune_trials else ""),
                    "graph": result["graph"],
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "inputs larger than L2 (particles 4.3 GB/GPU)"},
@@ -489,9 +496,147 @@ def run_ours(args, rank, world, dist):
         line["e2e"] = result["e2e"]
     if "batched" in result:
         line["batched"] = result["batched"]
+    if world == 1 and not args.no_legs:
+        # short runs of the other synthetic configurations, so that one
+        # default run records them all (each after its own warm-up)
+        line["workloads"] = {}
+        for name, plain in (("small_cic_32", 0), ("laser_ramp", 0), ("foil_overdense", 0), ("khi_128", 2)):
+            leg = workload_leg(name, args.leg_steps, 3, plain_steps=plain)
+            line["workloads"][name] = leg
+            log(f"leg {name}: {leg['value']:.3e} {UNIT}, push+deposit {leg['push_deposit_ms']:.3f} ms")
     if world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline_oracle()
     return line
+
+
+# ----------------------------------------------------------------------------- one box over N GPUs
+
+def run_decomposed(args, rank, world, dist):
+    """The headline thermal box split into z slabs, one per rank (GPU); per
+    step each slab exchanges its J guard planes, the particles leaving
+    through its z faces and its E and B planes with the two neighbouring
+    slabs (NCCL point-to-point; a one-slab run exchanges with itself).
+    Push+deposit time = push kernel + J / migrant exchange + frame
+    maintenance, CUDA events on the slab's stream, max over ranks; the rate
+    is the whole box's particles over that time (strong scaling: the box is
+    fixed, the slabs shrink as N grows)."""
+    import torch
+
+    from paper_1606_02862_gb300 import build as libbuild
+    from paper_1606_02862_gb300 import decomp, pic, shard
+    from paper_1606_02862_gb300 import workloads as W
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if rank == 0 or not os.path.exists(pic.LIB_PATH):
+        libbuild.build()
+    if dist is not None:
+        dist.barrier()
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    n, ppc, u_th = args.n, 8, 0.05
+    sc = (8, 4, 4) if args.sc == "auto" else tuple(int(v) for v in args.sc.split("x"))
+    threads = args.threads or 256
+    layout = decomp.SlabLayout(n, world, sc[2])
+    z0, nzl = layout.extent(rank)
+    m = n * n * nzl * ppc
+    X = torch.empty((m, 3), dtype=torch.float64, pin_memory=True)
+    U = torch.empty((m, 3), dtype=torch.float64, pin_memory=True)
+    Wt = torch.empty((m,), dtype=torch.float64, pin_memory=True)
+    W.fill_thermal(X.numpy(), U.numpy(), Wt.numpy(), n, n, n, ppc, u_th, z_lo=z0, z_hi=z0 + nzl)
+    X[:, 2] -= z0
+    ring = decomp.DistRing(dist) if dist is not None else decomp.LocalRing(1)
+
+    def new_slab():
+        ctx = pic.Context([(n, n, nzl)], (1.0, 1.0, 1.0), W.DT_HALF_COURANT,
+                          [pic.Species(-1.0, 1.0, SHAPE[args.shape], True, GATHER[args.gather])],
+                          sc=sc, threads_per_sc=threads, use_graph=False)
+        ctx.set_background(0, 0.01)
+        slab = decomp.LibpicSlab(ctx)
+        load(ctx, X, U, Wt)
+        stepper = decomp.SlabStepper([slab], ring, decomp.torch_buffers("cuda"))
+        stepper.prime()
+        return ctx, stepper
+
+    ctx, stepper = new_slab()
+    stepper.step(args.warmup)
+    marks = {k: [] for k in ("push", "exchange", "frames", "fields", "end")}
+
+    def mark(label):
+        e = torch.cuda.Event(enable_timing=True)
+        e.record(stream)
+        marks[label].append(e)
+
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    hbm, hbm_src = measured_hbm()
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        stepper.step(args.steps, mark=mark)
+        ctx.sync()
+        torch.cuda.synchronize()
+
+    def span(a, b):
+        return sum(x.elapsed_time(y) for x, y in zip(marks[a], marks[b])) / args.steps
+
+    push_ms, exch_ms = span("push", "exchange"), span("exchange", "frames")
+    frames_ms, fields_ms = span("frames", "fields"), span("fields", "end")
+    step_ms = span("push", "end")
+    pd_ms = push_ms + exch_ms + frames_ms
+    pd_max, step_max, push_max = shard.max_over_ranks([pd_ms, step_ms, push_ms], dist, device="cuda")
+    npart = n ** 3 * ppc
+    mine_bytes = m * MIXED_BYTES_PER_PARTICLE + n * n * nzl * MIXED_BYTES_PER_CELL
+    achieved = mine_bytes / (push_ms * 1e-3) / 1e9
+    ctx.close()
+
+    # end to end: create, load from pinned host memory, K steps, read back
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    cap = m + m // 4 + 4096  # the slab's count drifts by the particles crossing its faces
+    Xo = torch.empty((cap, 3), dtype=torch.float64, pin_memory=True)
+    Uo = torch.empty((cap, 3), dtype=torch.float64, pin_memory=True)
+    Wo = torch.empty((cap,), dtype=torch.float64, pin_memory=True)
+    Eo = torch.empty((3, nzl, n, n), dtype=torch.float64, pin_memory=True).numpy()
+    t0 = time.perf_counter()
+    ctx, stepper = new_slab()
+    stepper.step(args.steps)
+    ctx.sync()
+    nout = ctx.read_particles_ptr(0, 0, cap, Xo.data_ptr(), Uo.data_ptr(), Wo.data_ptr())
+    ctx.read_fields_ptr(0, pic.FIELD_E, Eo.ctypes.data)
+    t_e2e = time.perf_counter() - t0
+    kernels = ctx.info(pic.INFO_KERNELS_PER_STEP)
+    ctx.close()
+    (t_max,) = shard.max_over_ranks([t_e2e], dist, device="cuda")
+    if rank != 0:
+        return None
+    return {
+        "metric": METRIC, "value": npart / (pd_max * 1e-3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_max, "higher_is_better": True,
+        "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": thermal_workload_name(args, n, ppc).replace(f"({npart} particles/GPU)",
+                                                                           f"({npart} particles)"),
+                   "form": f"mixed, supercell {'x'.join(map(str, sc))}, {threads} threads/supercell",
+                   "parallelism": f"domain decomposition: {world} z slabs of {layout.extent(0)[1]} "
+                                  "planes, NCCL point-to-point halo and particle exchange"
+                                  if world > 1 else "one slab exchanging with itself",
+                   "l2": "inputs larger than L2"},
+        "push_deposit_ms_per_step": pd_max,
+        "stage_ms_per_step": {"push_deposit_kernel": push_ms, "j_and_migrant_exchange": exch_ms,
+                              "frame_maintenance": frames_ms, "yee_with_exchanges": fields_ms},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": None, "kernel": "k_push_deposit (rank 0's slab)",
+                     "peak_source": hbm_src},
+        "gpu_launches": int(kernels * args.steps), "clocks": clk.summary(),
+        "e2e": {"value": npart * args.steps / t_max, "unit": UNIT,
+                "h2d_bytes_per_step": m * 56.0 / args.steps,
+                "d2h_bytes_per_step": (nout * 56.0 + Eo.nbytes) / args.steps, "seconds": t_max,
+                "what": "per rank: pic_create + load (pinned FP64 host) + K staged steps with exchanges "
+                        "+ read back particles and E, wall clock, max over ranks; bytes of rank 0"},
+    }
 
 
 # ----------------------------------------------------------------------------- other workloads
@@ -507,60 +652,88 @@ WORKLOADS = {
 }
 
 
-def run_workload(args):
-    """Push+deposit rate of one of the other synthetic workloads (mixed form,
-    graph replay, in-graph stage events), as its own JSON line."""
-    import torch
-
-    from paper_1606_02862_gb300 import build as libbuild
+def workload_leg(name, steps, warmup, sc=(8, 4, 4), threads=256, plain_steps=0, diag_every=0, log_fn=log):
+    """Push+deposit rate of one synthetic workload (mixed form, graph replay,
+    in-graph stage events) as a dict; plain_steps > 0 also times the plain
+    FP64 form (the paper runs its KHI case in single and double precision);
+    diag_every > 0 records the FP64 diagnostics every diag_every steps (the
+    timing then covers the steps between them)."""
     from paper_1606_02862_gb300 import pic
     from paper_1606_02862_gb300 import workloads as W
 
-    libbuild.build()
-    stream = torch.cuda.Stream()
-    torch.cuda.set_stream(stream)
     t0 = time.perf_counter()
-    wl = W.khi() if args.workload == "khi_128" else getattr(W, args.workload)()
-    log(f"generated {args.workload} in {time.perf_counter() - t0:.1f} s")
-    sc = (8, 4, 4) if args.sc == "auto" else tuple(int(v) for v in args.sc.split("x"))
-    threads = args.threads or 256
+    wl = W.khi() if name == "khi_128" else getattr(W, name)()
+    log_fn(f"generated {name} in {time.perf_counter() - t0:.1f} s")
     ctx = pic.from_workload(wl, sc=sc, threads_per_sc=threads)
     npart = sum(ctx.count_particles(b, s) for b in range(len(wl.boxes)) for s in range(len(wl.species))
                 if wl.species[s].mobile)
     ncell = wl.ncells
-    ctx.step(args.warmup)
+    ctx.step(warmup)
+    diags = []
     ctx.stage_timing(True)
-    ctx.step(args.steps)
+    if diag_every > 0:
+        diags.append([warmup] + ctx.diagnostics(0).tolist())
+        for k in range(0, steps, diag_every):
+            ctx.step(min(diag_every, steps - k))
+            diags.append([warmup + min(k + diag_every, steps)] + ctx.diagnostics(0).tolist())
+    else:
+        ctx.step(steps)
     ms, nst = ctx.stage_times()
     ctx.close()
-    plain = None
-    if args.workload == "khi_128" and not args.no_plain:
-        # the paper runs this workload in single and double precision
+    out = {"workload": f"{name}: {WORKLOADS[name]}", "particles": npart, "cells": ncell, "steps": nst,
+           "warmup": warmup, "value": npart / ((ms[0] + ms[1]) / nst * 1e-3), "unit": UNIT,
+           "push_deposit_ms": (ms[0] + ms[1]) / nst,
+           "stage_ms_per_step": {"push_deposit_kernel": ms[0] / nst, "frame_maintenance": ms[1] / nst,
+                                 "yee": ms[2] / nst},
+           "step_ms": ms[3] / nst,
+           "hbm_frac": (npart * MIXED_BYTES_PER_PARTICLE + ncell * MIXED_BYTES_PER_CELL)
+           / (ms[0] / nst * 1e-3) / 1e9 / measured_hbm()[0],
+           "form": f"mixed, supercell {'x'.join(map(str, sc))}, {threads} threads"}
+    if diags:
+        out["diagnostics"] = {"columns": ["step", "field_energy", "kinetic_energy", "charge",
+                                          "max_abs_divE_minus_rho"], "rows": diags}
+    if plain_steps > 0:
         pctx = pic.from_workload(wl, precision=pic.PRECISION_FP64_PLAIN)
         pctx.step(1)
         pctx.stage_timing(True)
-        pctx.step(args.plain_steps)
+        pctx.step(plain_steps)
         pms, pn = pctx.stage_times()
         pctx.close()
-        plain = {"value": npart / (pms[0] / pn * 1e-3), "unit": UNIT, "push_ms": pms[0] / pn,
-                 "step_ms": pms[3] / pn, "steps": pn}
+        out["plain_fp64"] = {"value": npart / (pms[0] / pn * 1e-3), "unit": UNIT, "push_ms": pms[0] / pn,
+                             "step_ms": pms[3] / pn, "steps": pn}
+        out["fp32_over_fp64_step"] = (pms[3] / pn) / (ms[3] / nst)
     del wl
-    pd = (ms[0] + ms[1]) / nst
+    return out
+
+
+def run_workload(args):
+    """One of the other synthetic workloads as its own JSON line."""
+    import torch
+
+    from paper_1606_02862_gb300 import build as libbuild
+
+    libbuild.build()
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    sc = (8, 4, 4) if args.sc == "auto" else tuple(int(v) for v in args.sc.split("x"))
+    threads = args.threads or 256
+    leg = workload_leg(args.workload, args.steps, args.warmup, sc, threads,
+                       plain_steps=0 if args.no_plain or args.workload != "khi_128" else args.plain_steps,
+                       diag_every=args.diag_every)
     hbm, hbm_src = measured_hbm()
-    achieved = (npart * MIXED_BYTES_PER_PARTICLE + ncell * MIXED_BYTES_PER_CELL) / (ms[0] / nst * 1e-3) / 1e9
-    return {"metric": METRIC, "value": npart / (pd * 1e-3), "unit": UNIT, "n_gpus": 1,
-            "steps": nst, "warmup": args.warmup, "ms_per_step": ms[3] / nst, "higher_is_better": True,
+    line = {"metric": METRIC, "value": leg["value"], "unit": UNIT, "n_gpus": 1,
+            "steps": leg["steps"], "warmup": args.warmup, "ms_per_step": leg["step_ms"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]} ({npart} particles, "
-                                   f"{ncell} cells)",
-                       "form": f"mixed, supercell {'x'.join(map(str, sc))}, {threads} threads"},
-            "stage_ms_per_step": {"push_deposit_kernel": ms[0] / nst, "frame_maintenance": ms[1] / nst,
-                                  "yee": ms[2] / nst},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": achieved / hbm, "traffic": None, "kernel": "k_push_deposit",
-                         "peak_source": hbm_src},
-            **({"plain_fp64": plain, "fp32_over_fp64": plain["step_ms"] and (plain["step_ms"] / (ms[3] / nst))}
-               if plain else {})}
+            "config": {"workload": f"{leg['workload']} ({leg['particles']} particles, {leg['cells']} cells)",
+                       "form": leg["form"]},
+            "stage_ms_per_step": leg["stage_ms_per_step"],
+            "roofline": {"bound": "hbm", "achieved": leg["hbm_frac"] * hbm, "peak": hbm, "unit": "GB/s",
+                         "frac": leg["hbm_frac"], "traffic": None, "kernel": "k_push_deposit",
+                         "peak_source": hbm_src}}
+    for k in ("plain_fp64", "fp32_over_fp64_step", "diagnostics"):
+        if k in leg:
+            line[k] = leg[k]
+    return line
 
 
 def run_yee(args):
@@ -716,7 +889,8 @@ def run_reference(args, rank):
             "data": "synthetic",
             "config": {"workload": thermal_workload_name(args, args.n),
                        "form": "FP64 CPU oracle, one host thread; each step a bounded sample (see cpu_baseline)"},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                             "cpu": cpu_model()},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -734,10 +908,20 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-legs", action="store_true",
+                    help="skip the short runs of the other configurations in the default line")
+    ap.add_argument("--leg-steps", type=int, default=20)
+    ap.add_argument("--diag-every", type=int, default=0,
+                    help="--workload runs: FP64 diagnostics every this many steps")
     ap.add_argument("--shape", default="tsc", choices=["tsc", "cic", "pcs"],
                     help="particle shape of the headline thermal workload")
     ap.add_argument("--gather", default="momentum", choices=["momentum", "energy"],
                     help="gather variant of the headline thermal workload")
+    ap.add_argument("--decomp", action="store_true",
+                    help="one box split into z slabs over the ranks (the default with --gpus > 1); "
+                         "with one GPU the single slab exchanges with itself")
+    ap.add_argument("--replicas", action="store_true",
+                    help="with --gpus > 1: one independent box per rank instead of one decomposed box")
     ap.add_argument("--workload", default="thermal_tsc_256",
                     choices=["thermal_tsc_256", "small_cic_32", "laser_ramp", "foil_overdense",
                              "khi_128", "laser_window", "yee"])
@@ -768,6 +952,8 @@ def main():
         line = run_yee(args) if rank == 0 else None
     elif args.workload != "thermal_tsc_256":
         line = run_workload(args) if rank == 0 else None
+    elif args.decomp or (world > 1 and not args.replicas):
+        line = run_decomposed(args, rank, world, dist)
     else:
         line = run_ours(args, rank, world, dist)
     if rank == 0 and line is not None:

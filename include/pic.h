@@ -100,8 +100,8 @@ enum { PIC_FIELD_E = 0, PIC_FIELD_B = 1, PIC_FIELD_J = 2, PIC_FIELD_RHO = 3 };
  * before the first step it times every configuration the push kernel is
  * built for that fits the boxes (sc 0,0,0: supercell shapes and thread
  * counts; threads_per_sc 0 with a given sc: thread counts) on the loaded
- * state itself -- push and frame maintenance of 3 steps after 2 warm-up
- * steps each, in side contexts on the context's stream and allocator -- and
+ * state itself -- push and frame maintenance over two sort periods after one
+ * warm-up step each, in side contexts on the context's stream and allocator -- and
  * moves the context into the fastest.  The result is kept for the process
  * and reused for states of the same kind (box sizes, species, particles per
  * cell).  Until then particles sit in 4 x 4 x 4 supercells.  pic_info

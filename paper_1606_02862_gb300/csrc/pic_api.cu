@@ -1599,7 +1599,9 @@ pic_status build_like(pic_ctx* c, const TuneCfg& cfg, const TuneSnapshot& snap, 
 }
 
 // Push + frame maintenance milliseconds per step of configuration cfg on
-// the snapshot (2 warm-up steps, then 3 timed with the step's stage events).
+// the snapshot: after one warm-up step (the sort pass that follows a load),
+// two whole sort periods timed with the step's stage events, so that sort
+// and stored-order passes weigh as they do in a run.
 double time_config(pic_ctx* c, const TuneCfg& cfg, const TuneSnapshot& snap)
 {
     pic_ctx* n = nullptr;
@@ -1607,8 +1609,8 @@ double time_config(pic_ctx* c, const TuneCfg& cfg, const TuneSnapshot& snap)
         return INFINITY;
     double ms[4] = {0, 0, 0, 0};
     int64_t k = 0;
-    const bool ok = pic_step(n, 2) == PIC_OK && pic_stage_timing(n, 1) == PIC_OK && pic_step(n, 3) == PIC_OK &&
-                    pic_stage_times(n, ms, &k) == PIC_OK && k > 0;
+    const bool ok = pic_step(n, 1) == PIC_OK && pic_stage_timing(n, 1) == PIC_OK &&
+                    pic_step(n, 2 * n->sort_every) == PIC_OK && pic_stage_times(n, ms, &k) == PIC_OK && k > 0;
     pic_destroy(n);
     cudaGetLastError();
     return ok ? (ms[0] + ms[1]) / (double)k : INFINITY;

@@ -22,33 +22,35 @@ def _bench():
 
 
 def test_committed_profile_has_every_figure():
+    import json
+
     bench = _bench()
-    vals = {}
     with open(bench.TRAFFIC_SUMMARY) as f:
-        for line in f:
-            if ":" in line and line.strip().startswith("- "):
-                k, v = line.strip()[2:].split(":", 1)
-                vals[k.strip()] = v.strip().strip("`")
-    assert len(vals["k_push.cu sha256"]) == 64
-    assert 60.0 < float(vals["dram bytes per particle"]) < 80.0   # 64.5 B algorithmic
-    assert 5.0 < float(vals["shared wavefronts per particle"]) < 40.0
-    assert float(vals["shared wavefronts per particle"]) < float(vals["l1 data-pipe wavefronts per particle"]) < 40.0
-    assert 100.0 < float(vals["fp32 operations per particle"]) < 3000.0
+        vals = json.load(f)
+    assert len(vals["kernel_source_sha256"]) == 64
+    assert 60.0 < float(vals["dram_bytes_per_particle"]) < 80.0   # 64.5 B algorithmic
+    assert 5.0 < float(vals["shared_wavefronts_per_particle"]) < 40.0
+    assert float(vals["shared_wavefronts_per_particle"]) < float(vals["l1_wavefronts_per_particle"]) < 40.0
+    assert 100.0 < float(vals["fp32_ops_per_particle"]) < 3000.0
+    assert "ncu" in vals["command"] and "--clock-control none" in vals["command"]
 
 
 def test_profile_is_used_only_for_the_kernel_it_was_taken_on(tmp_path, monkeypatch):
+    import json
+
     bench = _bench()
     src = tmp_path / "k_push.cu"
     src.write_bytes(b"// a kernel\n")
     sha = hashlib.sha256(src.read_bytes()).hexdigest()
-    md = tmp_path / "profile.md"
-    md.write_text(f"- k_push.cu sha256: `{sha}`\n- dram bytes per particle: `64.5`\n"
-                  f"- shared wavefronts per particle: `17.0`\n- fp32 operations per particle: `670`\n")
+    js = tmp_path / "profile.json"
+    fig = {"kernel_source_sha256": sha, "dram_bytes_per_particle": 64.5, "shared_wavefronts_per_particle": 17.0,
+           "fp32_ops_per_particle": 670}
+    js.write_text(json.dumps(fig))
     monkeypatch.setattr(bench, "PUSH_KERNEL_SRC", str(src))
-    monkeypatch.setattr(bench, "TRAFFIC_SUMMARY", str(md))
+    monkeypatch.setattr(bench, "TRAFFIC_SUMMARY", str(js))
     assert bench.push_profile() == {"tpp": 64.5, "wpp": 17.0, "fpp": 670.0, "wkind": "smem"}
     # the L1 data-pipe count, when present, is the one the binding roofline uses
-    md.write_text(md.read_text() + "- l1 data-pipe wavefronts per particle: `18.0`\n")
+    js.write_text(json.dumps(dict(fig, l1_wavefronts_per_particle=18.0)))
     assert bench.push_profile() == {"tpp": 64.5, "wpp": 18.0, "fpp": 670.0, "wkind": "l1"}
     src.write_bytes(b"// a changed kernel\n")
     assert bench.push_profile() == {"tpp": None, "wpp": None, "fpp": None, "wkind": None}
@@ -56,7 +58,7 @@ def test_profile_is_used_only_for_the_kernel_it_was_taken_on(tmp_path, monkeypat
 
 def test_missing_profile_gives_nones(tmp_path, monkeypatch):
     bench = _bench()
-    monkeypatch.setattr(bench, "TRAFFIC_SUMMARY", str(tmp_path / "absent.md"))
+    monkeypatch.setattr(bench, "TRAFFIC_SUMMARY", str(tmp_path / "absent.json"))
     assert bench.push_profile() == {"tpp": None, "wpp": None, "fpp": None, "wkind": None}
 
 

@@ -188,11 +188,35 @@ def test_open_y_rejected_in_plain_form():
         ctx.close()
 
 
+def _unmatched_near_faces(ctx, st, ny, excused, tol=1e-5):
+    """Particles present on one side only (FP32 and FP64 may disagree on a
+    face crossing by the rounding of the position): each must sit within tol
+    cells of a y face of the box it is still in, i.e. on the plane the other
+    side's copy crossed.  Returns the number newly found; `excused` keeps
+    (species, id) of every one found so far, which are left out afterwards."""
+    found = 0
+    for si, sp in enumerate(st.species):
+        p = ctx.read_particles(0, si, ids=True)
+        gpu = dict(zip(p["id"].tolist(), p["x"][:, 1].tolist()))
+        orc = dict(zip(sp.ids.tolist(), sp.x[:, 1].tolist()))
+        for side, mine, other in (("gpu", gpu, orc), ("oracle", orc, gpu)):
+            for i in set(mine) - set(other):
+                if (si, i) in excused:
+                    continue
+                y = mine[i]
+                assert min(abs(y), abs(y - ny)) <= tol, (side, si, i, y)
+                excused.add((si, i))
+                found += 1
+    return found
+
+
 def test_laser_window_run_matches_oracle(orc):
     """The open-boundary laser workload at reduced size through 70 steps with
     the window advanced by 4 cells whenever c t passes them (5 shifts) and the
-    same fresh plasma loaded on both sides: particle counts, charge, field
-    energy and E against the oracle run of the same recipe."""
+    same fresh plasma loaded on both sides: every particle by id (one present
+    on one side only must have crossed a y face within 1e-5 cells of it, the
+    FP32/FP64 disagreement on that crossing), charge, field energy and E
+    against the oracle run of the same recipe."""
     from paper_1606_02862_gb300 import pic
     from paper_1606_02862_gb300 import workloads as W
 
@@ -204,22 +228,29 @@ def test_laser_window_run_matches_oracle(orc):
     a = wl.extra["antenna"]
     bd = wl.extra["boundary"]
     species = []
+    next_id = []
     for sd, (x, u, w) in zip(wl.species, b.particles):
-        species.append(orc.Species(sd.q, sd.m, sd.shape, x, u, w))
+        osp = orc.Species(sd.q, sd.m, sd.shape, x, u, w)
+        osp.ids = np.arange(x.shape[0])  # the library's ids: load order per species
+        next_id.append(x.shape[0])
+        species.append(osp)
     st = orc.State(b.nx, b.ny, b.nz, wl.dt, species=species, open_y=True,
                    absorber=(bd["absorber_cells"], bd["absorber_sigma"]),
                    antenna=orc.Antenna(ja=a["plane_y"], E0=a["E0"], omega=a["omega"], w0=a["w0"],
                                        xc=a["xc"], zc=a["zc"], tau=a["tau"], t0=a["t0"]))
     rng = np.random.default_rng(77)
     shifts = 0
+    excused = set()
     try:
         for k in range(70):
             ctx.step(1)
             st.step(1)
+            _unmatched_near_faces(ctx, st, b.ny, excused)
             if (k + 1) * wl.dt >= (shifts + 1) * 4:
                 shifts += 1
                 ctx.shift_window(0, 4)
                 st.shift_window(4)
+                _unmatched_near_faces(ctx, st, b.ny, excused)
                 slab = W.window_slab(rng, b.nx, b.nz, b.ny - 4, b.ny, 2, wl.extra["density"],
                                      y_shift=float(4 * shifts))
                 for si, (x, u, w) in enumerate(slab):
@@ -228,14 +259,20 @@ def test_laser_window_run_matches_oracle(orc):
                     sp.x = np.vstack([sp.x, x])
                     sp.u = np.vstack([sp.u, u])
                     sp.w = np.concatenate([sp.w, w])
+                    sp.ids = np.concatenate([sp.ids, np.arange(next_id[si], next_id[si] + x.shape[0])])
+                    next_id[si] += x.shape[0]
         assert shifts == 5
+        print("particles on one side only (all at a y face):", sorted(excused))
         for si in range(2):
+            gone = sum(1 for s_, _ in excused if s_ == si)
             n_gpu, n_orc = ctx.count_particles(0, si), st.species[si].x.shape[0]
-            assert abs(n_gpu - n_orc) <= 2, (si, n_gpu, n_orc)
+            assert abs(n_gpu - n_orc) <= gone, (si, n_gpu, n_orc, gone)
         d_gpu, d_orc = ctx.diagnostics(0), st.diagnostics()
         print("laser window run: gpu", d_gpu, "oracle", d_orc)
         assert abs(d_gpu[0] / d_orc[0] - 1) < 1e-3
-        assert abs(d_gpu[2] - d_orc[2]) < 1e-6 * max(1.0, abs(d_orc[2])) + 2 * 0.01
+        qw_max = max(abs(sp.q) * float(np.max(np.abs(sp.w))) for sp in st.species)
+        # the particles found above, plus the FP32 rounding of every weight
+        assert abs(d_gpu[2] - d_orc[2]) < 1e-6 * max(1.0, abs(d_orc[2])) + max(2, len(excused)) * qw_max
         E = ctx.read_fields(0, pic.FIELD_E)
         assert np.max(np.abs(E - st.E)) < 1e-3 * np.max(np.abs(st.E))
     finally:
