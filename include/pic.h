@@ -49,7 +49,8 @@ typedef enum {
     PIC_ERR_OOM = 3,        /* the device allocator returned NULL */
     PIC_ERR_CUDA = 4,       /* a CUDA runtime call failed (message in pic_last_error) */
     PIC_ERR_FRAME_POOL = 5, /* the frame pool ran out of free frames during a step */
-    PIC_ERR_TIMEOUT = 6,    /* a bounded device-side wait gave up (reserved: no kernel waits today) */
+    PIC_ERR_TIMEOUT = 6,    /* a bounded device-side wait gave up (the push kernel waits ~2 s at most
+                               for each of its tensor and bulk copies into shared memory) */
     PIC_ERR_STATE = 7,      /* the context is poisoned by an earlier error */
     PIC_ERR_CAPACITY = 8,   /* the per-step buffer of particles changing supercell overflowed */
     PIC_ERR_PARTICLE = 9    /* a particle produced a non-finite momentum or position */
@@ -153,7 +154,9 @@ pic_status pic_create(const pic_grid* grids, int32_t nboxes, const double dx[3],
 /*
  * pic_set_background -- a fixed, uniform charge density rho_bg for box `box`
  * (a neutralising background).  It adds to the charge density of the
- * diagnostics and carries no current.
+ * diagnostics and carries no current.  Not in the paper (its runs load
+ * electrons and ions, Sec. 4); a single-species plasma needs it to start
+ * from zero fields consistently with Gauss's law.
  */
 pic_status pic_set_background(pic_ctx* ctx, int32_t box, double rho_bg);
 
@@ -215,7 +218,10 @@ pic_status pic_set_antenna(pic_ctx* ctx, int32_t box, const pic_antenna* a);
 pic_status pic_shift_window(pic_ctx* ctx, int32_t box, int32_t cells);
 
 /*
- * pic_load_particles -- append n particles of species `species` to box `box`.
+ * pic_load_particles -- append n particles of species `species` to box `box`
+ * (Sec. 2.1: macro particles live in a continuous domain over the cells and
+ * are kept in frames of as many particles as their supercell has cells; this
+ * call places each into a frame of the supercell holding its position).
  *   x[n*3]  global positions in cell units (host, FP64); wrapped
  *           periodically into [0, N) on load.
  *   u[n*3]  momenta u = gamma v, taken as u^{n-1/2} of the next step.
@@ -232,12 +238,16 @@ pic_status pic_load_particles(pic_ctx* ctx, int32_t box, int32_t species, int64_
 
 /*
  * pic_write_fields -- overwrite field `which` (PIC_FIELD_E or PIC_FIELD_B) of
- * box `box` from f[3*nz*ny*nx] (host, FP64, component-major, x fastest).
+ * box `box` from f[3*nz*ny*nx] (host, FP64, component-major, x fastest), at
+ * the Yee positions of the file header (Sec. 2.1: the fields live on the grid
+ * of cells; Sec. 4: the Yee field solver).
  */
 pic_status pic_write_fields(pic_ctx* ctx, int32_t box, int32_t which, const double* f);
 
 /*
- * pic_step -- advance every box by nsteps full PIC cycles (step order above).
+ * pic_step -- advance every box by nsteps full PIC cycles (step order above;
+ * Sec. 4 names the cycle's algorithms: Boris pusher, Esirkepov current
+ * solver, Yee field solver, TSC interpolation).
  * Blocks until the device finished, then checks the device status word:
  * PIC_ERR_FRAME_POOL, PIC_ERR_CAPACITY, PIC_ERR_PARTICLE or PIC_ERR_TIMEOUT
  * report a condition raised by a kernel.
@@ -250,11 +260,13 @@ pic_status pic_step(pic_ctx* ctx, int32_t nsteps);
  */
 pic_status pic_step_async(pic_ctx* ctx, int32_t nsteps);
 
-/* pic_sync -- wait for the context's stream and check the device status word. */
+/* pic_sync -- wait for the context's stream and check the device status word (the cycle of
+ * pic_step, Sec. 4). */
 pic_status pic_sync(pic_ctx* ctx);
 
 /*
- * pic_read_fields -- copy field `which` of box `box` into out[3*nz*ny*nx]
+ * pic_read_fields (Sec. 2.1 fields on the grid of cells; J is the Esirkepov
+ * current of Sec. 4) -- copy field `which` of box `box` into out[3*nz*ny*nx]
  * (PIC_FIELD_E, _B, _J) or out[nz*ny*nx] (PIC_FIELD_RHO, the charge density
  * at the nodes including the background), host, FP64, x fastest.  J is the
  * current of the last step (J^{n+1/2}).  Mixed form, E/B/J: a page-locked
@@ -263,12 +275,14 @@ pic_status pic_sync(pic_ctx* ctx);
 pic_status pic_read_fields(pic_ctx* ctx, int32_t box, int32_t which, double* out);
 
 /*
- * pic_count_particles -- number of particles of (box, species) into *n_out.
+ * pic_count_particles -- number of particles of (box, species) into *n_out
+ * (the sum of the counts of the species' frame lists, Sec. 2.1).
  */
 pic_status pic_count_particles(pic_ctx* ctx, int32_t box, int32_t species, int64_t* n_out);
 
 /*
- * pic_read_particles -- copy the particles of (box, species) to host FP64
+ * pic_read_particles (Sec. 2.1: the frames of every supercell, in global
+ * coordinates) -- copy the particles of (box, species) to host FP64
  * arrays: x[cap*3] global positions in cell units, u[cap*3], w[cap]; id[cap]
  * (optional, NULL to skip; requires track_ids).  Any of x, u, w may be NULL
  * to skip it.  The order is unspecified (frames reorder particles).  *n_out
@@ -281,7 +295,9 @@ pic_status pic_read_particles(pic_ctx* ctx, int32_t box, int32_t species, int64_
                               double* x, double* u, double* w, int64_t* id, int64_t* n_out);
 
 /*
- * pic_diagnostics -- FP64 reductions of box `box` into out[4]:
+ * pic_diagnostics -- FP64 reductions of box `box` into out[4] (the paper
+ * prints none; these check what the step of Sec. 4 conserves: energy, charge,
+ * and Gauss's law, which the charge-conserving Esirkepov current keeps):
  *   out[0] field energy   sum over cells of (E^2 + B^2)/2 * dx dy dz,
  *   out[1] kinetic energy sum over particles of w m (gamma - 1),
  *   out[2] total charge   sum of q w plus rho_bg * volume,
@@ -291,7 +307,8 @@ pic_status pic_read_particles(pic_ctx* ctx, int32_t box, int32_t species, int64_
 pic_status pic_diagnostics(pic_ctx* ctx, int32_t box, double out[4]);
 
 /*
- * pic_stage_times -- device time in milliseconds of each stage of the last
+ * pic_stage_times (a measurement service: the paper compares runtimes of the
+ * step, Sec. 4) -- device time in milliseconds of each stage of the last
  * nsteps pic_step calls since pic_stage_timing(ctx, 1) (CUDA events on the
  * context's stream): ms[0] push+deposit, ms[1] frame maintenance,
  * ms[2] Yee update (with the J fold), ms[3] whole step; *nsteps_out
@@ -302,7 +319,8 @@ pic_status pic_stage_timing(pic_ctx* ctx, int32_t enable);
 pic_status pic_stage_times(pic_ctx* ctx, double ms[4], int64_t* nsteps_out);
 
 /*
- * pic_info -- one integer property of the context into *out:
+ * pic_info (a service of this library; no counterpart in the paper) -- one
+ * integer property of the context into *out:
  *   PIC_INFO_GRAPH_ACTIVE    1 if pic_step replays captured CUDA graphs (mixed form,
  *                            after the first step), else 0;
  *   PIC_INFO_KERNELS_PER_STEP number of libpic kernel launches one step makes (for a
@@ -466,10 +484,10 @@ pic_status pic_migrants_accept(pic_ctx* ctx, int32_t side, const void* buf);
 pic_status pic_field_energy_noalloc(const double* E, const double* B, int64_t ncells,
                                     double cell_volume, double* out, void* stream);
 
-/* pic_last_error -- human-readable message of the last error (never NULL). */
+/* pic_last_error -- human-readable message of the last error (never NULL); an ABI service. */
 const char* pic_last_error(const pic_ctx* ctx);
 
-/* pic_destroy -- release every resource of the context; NULL is a no-op. */
+/* pic_destroy -- release every resource of the context; NULL is a no-op; an ABI service. */
 void pic_destroy(pic_ctx* ctx);
 
 #ifdef __cplusplus

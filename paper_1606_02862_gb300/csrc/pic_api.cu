@@ -74,6 +74,7 @@ struct pic_ctx {
     int push_grid = 0;
     std::vector<BoxDev> boxes_h;
     BoxDev* boxes_d = nullptr;
+    CUtensorMap* tmaps_d = nullptr;  // [nboxes][2] E, B tile maps of the push
     int* sc_box_d = nullptr;
     int* items_d = nullptr;
     int* yee_off_d = nullptr;
@@ -358,6 +359,7 @@ StepDev make_step(const pic_ctx* c, int parity)
     for (int a = 0; a < 3; ++a)
         d.move[a] = (float)(c->dt / c->h[a]);
     d.boxes = c->boxes_d;
+    d.tmaps = c->tmaps_d;
     d.sc_box = c->sc_box_d;
     d.items = c->items_d;
     const double V = c->h[0] * c->h[1] * c->h[2];
@@ -527,7 +529,7 @@ YeePlan yee_plan(const pic_ctx* c)
     return YeePlan{c->boxes_d, c->yee_off_d, c->nboxes, c->yee_nblocks, (float)c->dt,
                    {(float)(1.0 / c->h[0]), (float)(1.0 / c->h[1]), (float)(1.0 / c->h[2])},
                    c->step_no, c->dt, {c->h[0], c->h[1], c->h[2]}, c->abs_off_d, c->abs_nblocks,
-                   c->any_antenna ? 1 : 0, c->guard};
+                   c->any_antenna ? 1 : 0, c->guard, c->sub_z ? 1 : 0};
 }
 
 // One stage of the mixed-form step (PIC_STAGE_*) on frame-table parity
@@ -804,6 +806,55 @@ int ilog2(int v)
 
 namespace {
 
+// TMA descriptors of the push's E/B tile loads, one per box and field: the
+// padded field array as a 4D tensor (x, y, z, component), box = the tile
+// (row pitch px, ty rows, tz planes, 3 components), so that one load brings
+// a supercell's three components into shared memory.  Reads past the array
+// (the pitch beyond the last tile's edge) come back as zeros.
+pic_status encode_tile_maps(pic_ctx* c)
+{
+    using Encode = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    static Encode encode = [] {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            fn = nullptr;
+        }
+        return reinterpret_cast<Encode>(fn);
+    }();
+    if (!encode)
+        return fail(c, PIC_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    int bpx = 0, bty = 0, btz = 0;
+    push_tile_box(c->LX, c->LY, c->LZ, c->guard, &bpx, &bty, &btz);
+    std::vector<CUtensorMap> maps((size_t)2 * c->nboxes);
+    for (int b = 0; b < c->nboxes; ++b) {
+        const BoxDev& bd = c->boxes_h[b];
+        const cuuint64_t dims[4] = {(cuuint64_t)bd.px, (cuuint64_t)bd.py, (cuuint64_t)bd.pz, 3};
+        const cuuint64_t strides[3] = {(cuuint64_t)bd.px * 4, (cuuint64_t)bd.px * bd.py * 4,
+                                       (cuuint64_t)padded_cells(bd) * 4};
+        const cuuint32_t box[4] = {(cuuint32_t)bpx, (cuuint32_t)bty, (cuuint32_t)btz, 3};
+        const cuuint32_t estr[4] = {1, 1, 1, 1};
+        for (int f = 0; f < 2; ++f) {
+            const CUresult r = encode(&maps[2 * b + f], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, f == 0 ? bd.E : bd.B,
+                                      dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                      CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (r != CUDA_SUCCESS)
+                return fail(c, PIC_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d) for box %d", (int)r, b);
+        }
+    }
+    CKS(dalloc(c, &c->tmaps_d, 2 * c->nboxes, false));
+    CK(cudaMemcpyAsync(c->tmaps_d, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice,
+                       c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return PIC_OK;
+}
+
 // Copy the host box table (open-y options included) to the device and
 // rebuild the absorber's block table; a change of the absorber's launch
 // shape drops the captured graphs.
@@ -1026,6 +1077,9 @@ pic_status pic_create(const pic_grid* grids, int32_t nboxes, const double dx[3],
             cudaGetLastError();
             return bail(PIC_ERR_CUDA);
         }
+        const pic_status mst = encode_tile_maps(c);
+        if (mst != PIC_OK)
+            return bail(mst);
     }
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
         cudaGetLastError();

@@ -33,6 +33,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda.h>  // CUtensorMap (type only; maps are encoded through the runtime's driver entry point)
 #include <cuda_runtime.h>
 
 namespace pic {
@@ -91,6 +92,7 @@ struct StepDev {
     float dt;
     float move[3];            // dt / h_d
     const BoxDev* boxes;      // [nboxes]
+    const CUtensorMap* tmaps; // [nboxes][2]: the E and B tile loads of the push (TMA)
     const int* sc_box;        // [nsc] box of each global supercell
     const int* items;         // [nsc] supercells in work order
     SpeciesDev sp[kMaxSpecies];
@@ -195,8 +197,11 @@ struct YeePlan {
     int abs_nblocks;
     int antenna;               // nonzero: some box has an antenna (launch k_antenna)
     int guard;                 // field guard cells below the interior (1 or 2)
+    int sub_z;                 // the (single) box is a subdomain slab: J is not folded in z
 };
 cudaError_t configure_push(int LX, int LY, int LZ, int threads, int guard, int* per_sm);
+// the E/B tile the push stages per supercell: row pitch px (floats), ty rows, tz planes
+void push_tile_box(int LX, int LY, int LZ, int guard, int* px, int* ty, int* tz);
 cudaError_t launch_push_deposit(const StepDev& d, int threads, int grid, cudaStream_t st);
 int push_supported(int LX, int LY, int LZ, int threads, int guard);
 size_t push_smem_bytes(int LX, int LY, int LZ, int threads, int guard);
