@@ -199,12 +199,12 @@ SHAPE = {"tsc": 2, "cic": 1, "pcs": 3}
 GATHER = {"momentum": 0, "energy": 1}
 
 
-def new_ctx(pic, n, precision, sc, threads, shape=2, gather=0):
+def new_ctx(pic, n, precision, sc, threads, shape=2, gather=0, sort_every=0):
     from paper_1606_02862_gb300 import workloads as W
 
     ctx = pic.Context([(n, n, n)], (1.0, 1.0, 1.0), W.DT_HALF_COURANT,
                       [pic.Species(-1.0, 1.0, shape, True, gather)], precision=precision, sc=sc,
-                      threads_per_sc=threads, use_graph=True)
+                      threads_per_sc=threads, use_graph=True, sort_every=sort_every)
     ctx.set_background(0, 0.01)
     return ctx
 
@@ -353,7 +353,8 @@ def run_ours(args, rank, world, dist):
     result = {}
 
     # ---------------- mixed form, device-resident inputs, graph replay
-    ctx = new_ctx(pic, n, pic.PRECISION_MIXED, sc, threads, SHAPE[args.shape], GATHER[args.gather])
+    ctx = new_ctx(pic, n, pic.PRECISION_MIXED, sc, threads, SHAPE[args.shape], GATHER[args.gather],
+                  args.sort_every)
     t0 = time.perf_counter()
     load(ctx, X, U, Wt)
     log(f"[rank {rank}] loaded in {time.perf_counter() - t0:.1f} s")
@@ -500,10 +501,11 @@ def run_ours(args, rank, world, dist):
         # short runs of the other synthetic configurations, so that one
         # default run records them all (each after its own warm-up)
         line["workloads"] = {}
-        for name, plain in (("small_cic_32", 0), ("laser_ramp", 0), ("foil_overdense", 0), ("khi_128", 2)):
+        for name, plain in (("small_cic_32", 5), ("laser_ramp", 2), ("foil_overdense", 2), ("khi_128", 2)):
             leg = workload_leg(name, args.leg_steps, 3, plain_steps=plain)
             line["workloads"][name] = leg
-            log(f"leg {name}: {leg['value']:.3e} {UNIT}, push+deposit {leg['push_deposit_ms']:.3f} ms")
+            log(f"leg {name}: {leg['value']:.3e} {UNIT}, push+deposit {leg['push_deposit_ms']:.3f} ms, "
+                f"plain FP64 {leg['plain_fp64']['value']:.3e}")
     if world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline_oracle()
     return line
@@ -700,7 +702,9 @@ def workload_leg(name, steps, warmup, sc=(8, 4, 4), threads=256, plain_steps=0, 
         pms, pn = pctx.stage_times()
         pctx.close()
         out["plain_fp64"] = {"value": npart / (pms[0] / pn * 1e-3), "unit": UNIT, "push_ms": pms[0] / pn,
-                             "step_ms": pms[3] / pn, "steps": pn}
+                             "step_ms": pms[3] / pn, "steps": pn,
+                             "hbm_frac": (npart * PLAIN_BYTES_PER_PARTICLE + ncell * PLAIN_BYTES_PER_CELL)
+                             / (pms[0] / pn * 1e-3) / 1e9 / measured_hbm()[0]}
         out["fp32_over_fp64_step"] = (pms[3] / pn) / (ms[3] / nst)
     del wl
     return out
@@ -911,6 +915,8 @@ def main():
     ap.add_argument("--no-legs", action="store_true",
                     help="skip the short runs of the other configurations in the default line")
     ap.add_argument("--leg-steps", type=int, default=20)
+    ap.add_argument("--sort-every", type=int, default=0,
+                    help="steps between sort passes of the push (0: the library's default, 4)")
     ap.add_argument("--diag-every", type=int, default=0,
                     help="--workload runs: FP64 diagnostics every this many steps")
     ap.add_argument("--shape", default="tsc", choices=["tsc", "cic", "pcs"],

@@ -226,7 +226,9 @@ __global__ void __launch_bounds__(256) k_antenna(const YeeArgs a)
     }
 }
 
-template <int G>
+// FOLD_Z false: the boxes are subdomain slabs, whose z guards went to their
+// neighbours (and theirs came in as additions): no z images to fold.
+template <int G, bool FOLD_Z>
 __global__ void __launch_bounds__(256, 4) k_yee_e(const YeeArgs a)
 {
     const BoxDev* bp;
@@ -258,9 +260,7 @@ __global__ void __launch_bounds__(256, 4) k_yee_e(const YeeArgs a)
     for (int q = 0; q < kYeeZ; ++q) {
         const int64_t i = pidx<G>(b, c.x, c.y, z0 + q);
         int iz[2];
-        // a subdomain slab's z guards went to its neighbours (and theirs came
-        // in as additions): no z images to fold there
-        const int nz = b.sub_z ? (iz[0] = z0 + q, 1) : images(z0 + q, b.nz, G, GuardsOf<G>::hyz, iz);
+        const int nz = FOLD_Z ? images(z0 + q, b.nz, G, GuardsOf<G>::hyz, iz) : (iz[0] = z0 + q, 1);
         // fold the J guard images into the interior
         jx[q] = 0.f;
         jy[q] = 0.f;
@@ -356,7 +356,8 @@ cudaError_t launch_yee_mixed_part(const YeePlan& p, int part, cudaStream_t st)
               p.step_no, p.dt_d, {p.dx_d[0], p.dx_d[1], p.dx_d[2]}};
     dim3 blk(32, 8);
     auto yb = p.guard == 2 ? k_yee_b<2> : k_yee_b<1>;
-    auto ye = p.guard == 2 ? k_yee_e<2> : k_yee_e<1>;
+    auto ye = p.guard == 2 ? (p.sub_z ? k_yee_e<2, false> : k_yee_e<2, true>)
+                           : (p.sub_z ? k_yee_e<1, false> : k_yee_e<1, true>);
     if (part == 0) {
         yb<<<p.nblocks, blk, 0, st>>>(a);
     } else if (part == 1) {
