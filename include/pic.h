@@ -119,6 +119,17 @@ typedef struct {
                                list by nearest node (TSC) / cell (CIC, PCS) and writes it back in that
                                order; the steps between push the lists in stored order; 0 = 4,
                                1 = sort on every step (results agree up to FP32 summation order) */
+    int32_t field_update;   /* mixed form, the field half of the step (Sec. 4, Yee solver):
+                               0 = a pic_step of two or more steps updates the fields of each pair
+                               of steps with one fused kernel per step that reads E, B, J from one
+                               buffer pair and writes E, B into a second one (allocated at the
+                               first step: 24 bytes per padded cell), so that the state is back in
+                               the first pair after every second step; an odd last step, and every
+                               pic_step_stage, uses the three in-place kernels;
+                               1 = the three in-place kernels (B half, E, B half) on every step,
+                               no second buffer pair.  Both give the same fields up to FP32
+                               rounding of the same operations. */
+    int32_t reserved;       /* 0 */
     int64_t pool_frames;    /* frame-pool capacity (mixed); 0 = sized at the first step from the load */
     int64_t move_capacity;  /* capacity of the per-step buffer of particles changing supercell; 0 = auto */
     /* Device allocator.  Both NULL: cudaMalloc / cudaFree.  Otherwise every
@@ -335,7 +346,11 @@ pic_status pic_stage_times(pic_ctx* ctx, double ms[4], int64_t* nsteps_out);
  *                            supercell the mixed form runs with (chosen by the library's
  *                            tuner once the first step began, when pic_options left them 0);
  *   PIC_INFO_TUNE_TRIALS     configurations the tuner timed for this context (0: given in
- *                            the options, or taken from an earlier tuning in this process).
+ *                            the options, or taken from an earlier tuning in this process);
+ *   PIC_INFO_FUSED_STEPS     steps since pic_create whose field update was the fused
+ *                            two-buffer kernel (pic_options.field_update 0).
+ * PIC_INFO_KERNELS_PER_STEP counts a step of a pic_step of two or more steps (with the
+ * fused field update when it is on: two launches fewer than the in-place kernels).
  */
 enum {
     PIC_INFO_GRAPH_ACTIVE = 0,
@@ -349,7 +364,8 @@ enum {
     PIC_INFO_SUPERCELL_Y = 8,
     PIC_INFO_SUPERCELL_Z = 9,
     PIC_INFO_THREADS = 10,
-    PIC_INFO_TUNE_TRIALS = 11
+    PIC_INFO_TUNE_TRIALS = 11,
+    PIC_INFO_FUSED_STEPS = 12
 };
 pic_status pic_info(pic_ctx* ctx, int32_t key, int64_t* out);
 

@@ -18,6 +18,7 @@
 // One launch covers all boxes: blocks of 32 x 8 cells in x-y, each thread
 // kYeeZ cells along z, box found from a per-box block offset table.
 #include "pic_internal.cuh"
+#include "tma.cuh"
 
 #include <algorithm>
 #include <cmath>
@@ -299,6 +300,333 @@ __global__ void __launch_bounds__(256, 4) k_yee_e(const YeeArgs a)
     }
 }
 
+// ------------------------------------------------------------ fused field update
+//
+// The whole field half of the cycle in one kernel, from one buffer pair into
+// the other: E^n, B^n and J are read from `src`, E^{n+1} and B^{n+1} (with
+// their periodic guard images) are written into `dst`, so that no value is
+// overwritten while a neighbouring cell still needs it.  Each block
+// z-marches an output tile of kFusedTX x kFusedTY cells through a chunk of
+// kFusedTZ planes.  Iteration s forms, with one block barrier after it,
+//   B^{n+1/2}(s+1) on the tile and one cell around it (E^n planes s+1, s+2),
+//   E^{n+1}(s)     on the tile and one cell above it in x and y
+//                  (B^{n+1/2} planes s-1, s: earlier iterations),
+//   B^{n+1}(s-2)   on the tile (E^{n+1} planes s-2, s-1: earlier iterations),
+// so the three stages of an iteration depend only on earlier iterations and
+// the intermediate B^{n+1/2} and E^{n+1} stay in shared memory; halo cells
+// are formed again by the neighbouring tiles (and the first planes of a
+// chunk by the chunk below).  The inputs of iteration s -- E^n(s+2), B^n(s+1)
+// and J(s), each a plane tile of the three components -- arrive by tensor
+// loads kFLook iterations ahead on one mbarrier; a thread waits for them and
+// otherwise touches global memory only for its stores and for the few J
+// guard images that fold into cells next to a box face.  HBM traffic per
+// cell: E^n, B^n, J read and E^{n+1}, B^{n+1} written, 60 bytes (the three
+// in-place kernels move 120); the halo rows come from L2.  The arithmetic of
+// every value is that of k_yee_b, k_yee_e, k_yee_b.
+constexpr int kFX = kFusedTX, kFY = kFusedTY, kFT = kFX * kFY;
+constexpr int kFEX = kFusedEX, kFEY = kFY + 3;  // plane tile: cells x0-G .. x0-G+35, y0-1 .. y0+kFY+1
+constexpr int kFSlot = ((3 * kFEY * kFEX + 31) / 32) * 32;  // floats, 128-byte slots
+constexpr unsigned kFBytes = 3u * kFEY * kFEX * 4u;         // bytes of one plane tile
+constexpr int kFLook = 3;                                    // bundles issued ahead
+constexpr int kFRE = 8, kFRB = 4;  // E^n slots (>= kFLook + 3); B^n, J slots and mbarriers (>= kFLook + 1)
+static_assert(kFRE >= kFLook + 3 && kFRB >= kFLook + 1 && !(kFRE & (kFRE - 1)) && !(kFRB & (kFRB - 1)),
+              "power-of-two rings deep enough for the look-ahead");
+constexpr int kHX = kFX + 2, kHY = kFY + 2, kHN = kHX * kHY;  // B^{n+1/2}: x0-1.., y0-1..
+constexpr int kEX = kFX + 1, kEY = kFY + 1, kEN = kEX * kEY;  // E^{n+1}: x0.., y0..
+constexpr int kHPer = (kHN + kFT - 1) / kFT, kEPer = (kEN + kFT - 1) / kFT;
+static_assert(kFEX >= kFX + 4 && kFEX % 4 == 0, "plane rows reach x0 + kFX + 2 from a 16-byte start");
+
+struct FusedSmem {
+    float en[kFRE][kFSlot];  // E^n plane tiles [c][y][x]
+    float bn[kFRB][kFSlot];  // B^n plane tiles
+    float jn[kFRB][kFSlot];  // J plane tiles (as deposited; guard images folded by the reader)
+    float bh[4][3][kHN];     // B^{n+1/2}, four planes [plane % 4][c][cell]
+    float e1[4][3][kEN];     // E^{n+1}, four planes [plane % 4][c][cell]
+    unsigned long long mb[kFRB];
+    int abort;
+};
+
+struct FusedArgs {
+    const BoxDev* src;
+    const BoxDev* dst;
+    const CUtensorMap* maps;  // [nboxes][3]: E, B, J plane maps over src
+    const int* blk_off;
+    int nboxes;
+    float dt, tau;  // tau = dt / 2
+    float ih[3];
+    unsigned* status;
+};
+
+int fused_blocks(int nx, int ny, int nz)
+{
+    return ((nx + kFX - 1) / kFX) * ((ny + kFY - 1) / kFY) * ((nz + kFusedTZ - 1) / kFusedTZ);
+}
+
+template <int G>
+__global__ void __launch_bounds__(kFT, 2) k_yee_fused(const FusedArgs a)
+{
+    extern __shared__ __align__(128) unsigned char fused_smem[];
+    FusedSmem& sm = *reinterpret_cast<FusedSmem*>(fused_smem);
+    const int box = find_box(a.blk_off, a.nboxes, blockIdx.x);
+    // the box's geometry and arrays in registers (stores through the field
+    // pointers could otherwise alias the table and force reloads)
+    const BoxDev& bt = a.src[box];
+    const int nx = bt.nx, ny = bt.ny, nz = bt.nz, px = bt.px, py = bt.py;
+    const int64_t pc = (int64_t)px * py * bt.pz;
+    const float* __restrict__ Jg = bt.J;
+    float* __restrict__ Eo = a.dst[box].E;
+    float* __restrict__ Bo = a.dst[box].B;
+    constexpr int hx = GuardsOf<G>::hx, hyz = GuardsOf<G>::hyz;
+    auto at = [&](int x, int y, int z) { return ((int64_t)(z + G) * py + (y + G)) * px + (x + G); };
+    // the three components of interior cell (x, y, z) and of its guard images
+    auto store3 = [&](float* F, int x, int y, int z, float v0, float v1, float v2) {
+        int ix[2], iy[2], iz[2];
+        const int cx = images(x, nx, G, hx, ix), cy = images(y, ny, G, hyz, iy), cz = images(z, nz, G, hyz, iz);
+#pragma unroll
+        for (int k = 0; k < 2; ++k)
+#pragma unroll
+            for (int j = 0; j < 2; ++j)
+#pragma unroll
+                for (int i = 0; i < 2; ++i)
+                    if (k < cz && j < cy && i < cx) {
+                        const int64_t g = at(ix[i], iy[j], iz[k]);
+                        F[g] = v0;
+                        F[pc + g] = v1;
+                        F[2 * pc + g] = v2;
+                    }
+    };
+    // interior cells away from every face have no images: one store each
+    const int64_t plane = (int64_t)px * py;
+    auto store3_fast = [&](float* F, bool col_plain, int64_t col, int x, int y, int z, float v0, float v1,
+                           float v2) {
+        if (col_plain && z >= hyz && z < nz - G) {
+            const int64_t g = (int64_t)(z + G) * plane + col;
+            F[g] = v0;
+            F[pc + g] = v1;
+            F[2 * pc + g] = v2;
+        } else {
+            store3(F, x, y, z, v0, v1, v2);
+        }
+    };
+    const int local = blockIdx.x - a.blk_off[box];
+    const int ntx = (nx + kFX - 1) / kFX, nty = (ny + kFY - 1) / kFY;
+    const int x0 = (local % ntx) * kFX, y0 = ((local / ntx) % nty) * kFY;
+    const int zc0 = (local / (ntx * nty)) * kFusedTZ, zc1 = min(zc0 + kFusedTZ, nz);
+    const int tid = threadIdx.x;
+    const CUtensorMap* maps = a.maps + 3 * box;
+    // bundle k (k0 .. zc1 + 1): E^n(k+2) while k+2 <= zc1+1, B^n(k+1) while
+    // zc0-1 <= k+1 <= zc1, J(k) while zc0 <= k <= zc1; E^n in slot
+    // (k - k0) % kFRE, B^n and J in slot (k - k0) % kFRB, completing on that
+    // slot's mbarrier as its ((k - k0) / kFRB)-th phase
+    const int k0 = zc0 - 3, klast = zc1 + 1;
+    int kiss = k0 - 1;  // tid 0: the last bundle issued
+    auto issue = [&](int k) {
+        kiss = k;
+        const int e = (k - k0) & (kFRE - 1), r = (k - k0) & (kFRB - 1);
+        const bool le = k + 2 <= zc1 + 1, lb = k + 1 >= zc0 - 1 && k + 1 <= zc1, lj = k >= zc0 && k <= zc1;
+        unsigned long long* mb = &sm.mb[r];
+        mbar_expect_tx(mb, kFBytes * ((le ? 1u : 0u) + (lb ? 1u : 0u) + (lj ? 1u : 0u)));
+        if (le)
+            tma_load_tile(sm.en[e], maps + 0, x0, y0 - 1 + G, k + 2 + G, mb);
+        if (lb)
+            tma_load_tile(sm.bn[r], maps + 1, x0, y0 - 1 + G, k + 1 + G, mb);
+        if (lj)
+            tma_load_tile(sm.jn[r], maps + 2, x0, y0 - 1 + G, k + G, mb);
+    };
+    if (tid == 0) {
+        for (int r = 0; r < kFRB; ++r)
+            mbar_init(&sm.mb[r], 1);
+        fence_mbar_init();
+        sm.abort = 0;
+        for (int k = k0; k <= min(k0 + kFLook, klast); ++k)
+            issue(k);
+    }
+    // J of the guard images of this thread's E^{n+1} cells other than the
+    // position itself (zero away from the box faces), one plane ahead
+    // (a column x, y inside [hx, nx - G) x [hyz, ny - G) and a plane inside
+    // [hyz, nz - G) have no images: most cells skip at once)
+    const auto inner = [](int v, int n, int h) { return v >= h && v < n - G; };
+    bool col_plain[kEPer], col_in[kEPer];
+#pragma unroll
+    for (int k = 0; k < kEPer; ++k) {
+        const int i = tid + k * kFT;
+        col_plain[k] = inner(x0 + i % kEX, nx, hx) && inner(y0 + i / kEX, ny, hyz);
+        col_in[k] = i < kEN && x0 + i % kEX <= nx && y0 + i / kEX <= ny;
+    }
+    auto fold_extra = [&](int s, float (&v)[kEPer][3]) {
+        const bool plane_plain = inner(s, nz, hyz) || s < zc0 || s > zc1;
+#pragma unroll
+        for (int k = 0; k < kEPer; ++k) {
+            v[k][0] = v[k][1] = v[k][2] = 0.0f;
+            if ((col_plain[k] && plane_plain) || !col_in[k] || s < zc0 || s > zc1)
+                continue;
+            const int i = tid + k * kFT;
+            const int x = x0 + i % kEX, y = y0 + i / kEX;
+            int ix[2], iy[2], iz[2];
+            const int cx = images(x < nx ? x : x - nx, nx, G, hx, ix);
+            const int cy = images(y < ny ? y : y - ny, ny, G, hyz, iy);
+            const int cz = images(s < nz ? s : s - nz, nz, G, hyz, iz);
+            if (cx == 1 && cy == 1 && cz == 1)
+                continue;
+#pragma unroll
+            for (int kk = 0; kk < 2; ++kk)
+#pragma unroll
+                for (int j = 0; j < 2; ++j)
+#pragma unroll
+                    for (int r = 0; r < 2; ++r)
+                        if (kk < cz && j < cy && r < cx && !(ix[r] == x && iy[j] == y && iz[kk] == s)) {
+                            const int64_t g = at(ix[r], iy[j], iz[kk]);
+                            v[k][0] += __ldg(Jg + g);
+                            v[k][1] += __ldg(Jg + pc + g);
+                            v[k][2] += __ldg(Jg + 2 * pc + g);
+                        }
+        }
+    };
+    float jx[kEPer][3] = {}, jxn[kEPer][3] = {};
+    __syncthreads();  // the mbarriers are initialised
+    // bundle k0 (E^n(zc0-1) alone) before the loop, and a barrier after it:
+    // its mbarrier is re-armed by the first iteration, for bundle k0 + kFRB
+    bool timed_out = !mbar_wait(&sm.mb[0], 0u);
+    __syncthreads();
+
+    constexpr int EC = kFEY * kFEX;
+    const float ih0 = a.ih[0], ih1 = a.ih[1], ih2 = a.ih[2], dt = a.dt, tau = a.tau;
+    // this thread's cells, the same in every plane: stage 1 cells i1 (tile
+    // index e1), stage 2 cells (tile index e2, B^{n+1/2} index h2, stored
+    // when st2), stage 3 cell (E^{n+1} index e3, B^{n+1/2} index h3)
+    int e1[kHPer], e2[kEPer], h2[kEPer];
+    bool st2[kEPer];
+    int64_t col2[kEPer];
+    // (the stage 1 cells past the first kFT go to the last threads and the
+    // stage 2 ones to the first, so that no warp takes both)
+    int i1[kHPer];
+#pragma unroll
+    for (int k = 0; k < kHPer; ++k) {
+        const int i = k == 0 ? tid : k * kFT + (kFT - 1 - tid);
+        i1[k] = i;
+        e1[k] = (i / kHX) * kFEX + i % kHX + G - 1;
+    }
+#pragma unroll
+    for (int k = 0; k < kEPer; ++k) {
+        const int i = tid + k * kFT, rx = i % kEX, ry = i / kEX;
+        h2[k] = (ry + 1) * kHX + rx + 1;
+        e2[k] = (ry + 1) * kFEX + rx + G;
+        st2[k] = i < kEN && rx < kFX && ry < kFY && x0 + rx < nx && y0 + ry < ny;
+        col2[k] = (int64_t)(y0 + ry + G) * px + (x0 + rx + G);
+    }
+    const int rx3 = tid % kFX, ry3 = tid / kFX;
+    const int e3 = ry3 * kEX + rx3, h3 = (ry3 + 1) * kHX + rx3 + 1;
+    const bool st3 = x0 + rx3 < nx && y0 + ry3 < ny;
+    const bool plain3 = inner(x0 + rx3, nx, hx) && inner(y0 + ry3, ny, hyz);
+    const int64_t col3 = (int64_t)(y0 + ry3 + G) * px + (x0 + rx3 + G);
+    for (int s = zc0 - 2; s <= zc1 + 1; ++s) {
+        if (tid == 0 && s + kFLook <= klast) {
+            fence_proxy_async();  // the slots being refilled were read by generic loads
+            issue(s + kFLook);
+        }
+        if (s >= zc0 - 1)
+            fold_extra(s + 1, jxn);
+        // the bundle of iteration s; its mbarrier was re-armed (at the top of
+        // iteration s - kFRB + kFLook) only after every thread had waited on
+        // that mbarrier's previous bundle and passed the barrier after it
+        if (!mbar_wait(&sm.mb[(s - k0) & (kFRB - 1)], (unsigned)(((s - k0) / kFRB) & 1)))
+            timed_out = true;
+        if (timed_out)
+            sm.abort = 1;
+        // stage 1: B^{n+1/2}(s+1) = B^n - tau curl E^n
+        if (s + 1 >= zc0 - 1 && s + 1 <= zc1) {
+            const float* E1 = sm.en[(s - 1 - k0) & (kFRE - 1)];  // plane s+1 (bundle s-1)
+            const float* E2 = sm.en[(s - k0) & (kFRE - 1)];      // plane s+2 (bundle s)
+            const float* Bp = sm.bn[(s - k0) & (kFRB - 1)];      // B^n plane s+1
+            float* H = sm.bh[(s + 1) & 3][0];
+#pragma unroll
+            for (int k = 0; k < kHPer; ++k) {
+                const int i = i1[k];
+                if (i < kHN) {
+                    const int e = e1[k];  // cell (x, y) in the plane tiles
+                    const float ex = E1[e], ey = E1[EC + e], ez = E1[2 * EC + e];
+                    const float cx = (E1[2 * EC + e + kFEX] - ez) * ih1 - (E2[EC + e] - ey) * ih2;
+                    const float cy = (E2[e] - ex) * ih2 - (E1[2 * EC + e + 1] - ez) * ih0;
+                    const float cz = (E1[EC + e + 1] - ey) * ih0 - (E1[e + kFEX] - ex) * ih1;
+                    H[i] = Bp[e] - tau * cx;
+                    H[kHN + i] = Bp[EC + e] - tau * cy;
+                    H[2 * kHN + i] = Bp[2 * EC + e] - tau * cz;
+                }
+            }
+        }
+        // stage 2: E^{n+1}(s) = E^n + dt (curl B^{n+1/2} - J)
+        if (s >= zc0 && s <= zc1) {
+            const float* H = sm.bh[s & 3][0];          // plane s
+            const float* Hp = sm.bh[(s - 1) & 3][0];   // plane s - 1
+            const float* E0 = sm.en[(s - 2 - k0) & (kFRE - 1)];  // E^n plane s (bundle s-2)
+            const float* Jp = sm.jn[(s - k0) & (kFRB - 1)];      // J plane s
+            float* X = sm.e1[s & 3][0];
+#pragma unroll
+            for (int k = 0; k < kEPer; ++k) {
+                const int i = tid + k * kFT;
+                if (i < kEN) {
+                    const int h = h2[k], e = e2[k];
+                    const float bxv = H[h], byv = H[kHN + h], bzv = H[2 * kHN + h];
+                    const float cx = (bzv - H[2 * kHN + h - kHX]) * ih1 - (byv - Hp[kHN + h]) * ih2;
+                    const float cy = (bxv - Hp[h]) * ih2 - (bzv - H[2 * kHN + h - 1]) * ih0;
+                    const float cz = (byv - H[kHN + h - 1]) * ih0 - (bxv - H[h - kHX]) * ih1;
+                    const float nex = E0[e] + dt * (cx - (Jp[e] + jx[k][0]));
+                    const float ney = E0[EC + e] + dt * (cy - (Jp[EC + e] + jx[k][1]));
+                    const float nez = E0[2 * EC + e] + dt * (cz - (Jp[2 * EC + e] + jx[k][2]));
+                    X[i] = nex;
+                    X[kEN + i] = ney;
+                    X[2 * kEN + i] = nez;
+                    if (st2[k] && s < zc1)
+                        store3_fast(Eo, col_plain[k], col2[k], x0 + i % kEX, y0 + i / kEX, s, nex, ney, nez);
+                }
+            }
+        }
+        // stage 3: B^{n+1}(s-2) = B^{n+1/2} - tau curl E^{n+1}
+        if (s - 2 >= zc0 && s - 2 < zc1) {
+            if (st3) {
+                const float* X0 = sm.e1[(s - 2) & 3][0];  // plane s - 2
+                const float* X1 = sm.e1[(s - 1) & 3][0];  // plane s - 1
+                const float* Hq = sm.bh[(s - 2) & 3][0];  // plane s - 2
+                const int e = e3, h = h3;
+                const float ex = X0[e], ey = X0[kEN + e], ez = X0[2 * kEN + e];
+                const float cx = (X0[2 * kEN + e + kEX] - ez) * ih1 - (X1[kEN + e] - ey) * ih2;
+                const float cy = (X1[e] - ex) * ih2 - (X0[2 * kEN + e + 1] - ez) * ih0;
+                const float cz = (X0[kEN + e + 1] - ey) * ih0 - (X0[e + kEX] - ex) * ih1;
+                store3_fast(Bo, plain3, col3, x0 + rx3, y0 + ry3, s - 2, Hq[h] - tau * cx, Hq[kHN + h] - tau * cy,
+                            Hq[2 * kHN + h] - tau * cz);
+            }
+        }
+        __syncthreads();
+        if (sm.abort)
+            break;
+        if (s >= zc0 - 1)
+#pragma unroll
+            for (int k = 0; k < kEPer; ++k)
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+                    jx[k][c] = jxn[k][c];
+    }
+    if (sm.abort && tid == 0) {
+        atomicOr(a.status, ST_TIMEOUT);
+        // loads still in flight land before the block's shared memory goes
+        // away: the last bundle issued on each mbarrier
+        for (int k = max(k0, kiss - kFRB + 1); k <= kiss; ++k)
+            mbar_wait(&sm.mb[(k - k0) & (kFRB - 1)], (unsigned)(((k - k0) / kFRB) & 1));
+    }
+}
+
+size_t fused_smem_bytes() { return sizeof(FusedSmem); }
+
+cudaError_t configure_yee_fused()
+{
+    cudaError_t e = cudaFuncSetAttribute(k_yee_fused<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sizeof(FusedSmem));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_yee_fused<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sizeof(FusedSmem));
+    return e;
+}
+
 // y absorber: every E and B value whose staggered y position lies in a
 // damping layer is multiplied by exp(-sigma d^2) (d = depth in the layer, 0
 // at its inner edge, 1 at the face), images included.  Work: the 2A planes
@@ -381,6 +709,24 @@ cudaError_t launch_yee_mixed_plan(const YeePlan& p, cudaStream_t st)
             return e;
     }
     return cudaSuccess;
+}
+
+cudaError_t launch_yee_fused(const YeePlan& p, const FusedPlan& f, cudaStream_t st)
+{
+    if (p.antenna) {
+        YeeArgs ya{f.src, p.blk_off, p.nboxes, p.dt, {p.ih[0], p.ih[1], p.ih[2]},
+                   p.step_no, p.dt_d, {p.dx_d[0], p.dx_d[1], p.dx_d[2]}};
+        k_antenna<<<64, 256, 0, st>>>(ya);
+    }
+    FusedArgs a{f.src, f.dst, f.maps, f.blk_off, p.nboxes, p.dt, 0.5f * p.dt, {p.ih[0], p.ih[1], p.ih[2]},
+                f.status};
+    if (p.guard == 2)
+        k_yee_fused<2><<<f.nblocks, kFT, sizeof(FusedSmem), st>>>(a);
+    else
+        k_yee_fused<1><<<f.nblocks, kFT, sizeof(FusedSmem), st>>>(a);
+    if (p.abs_nblocks > 0)
+        k_absorb_y<<<p.abs_nblocks, 256, 0, st>>>(f.dst, p.abs_off, p.nboxes);
+    return cudaGetLastError();
 }
 
 // ------------------------------------------------------------ subdomain halos

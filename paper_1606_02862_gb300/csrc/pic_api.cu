@@ -130,8 +130,23 @@ struct pic_ctx {
     cudaGraph_t graph[2] = {nullptr, nullptr};
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
     cudaGraphNode_t evnode[2][4] = {};
-    cudaEvent_t placeholder[4] = {};
+    cudaEvent_t placeholder[8] = {};
     bool graph_failed = false;
+    // fused field update (pic_options.field_update 0): a second field buffer
+    // pair; a pair of steps goes first -> second -> first.  The tables, push
+    // maps and Yee maps of the second pair mirror those of the first.
+    bool fused_ready = false;
+    float *E_alt = nullptr, *B_alt = nullptr;
+    BoxDev* boxes_alt_d = nullptr;
+    CUtensorMap* tmaps_alt_d = nullptr;  // [nboxes][2] push tile maps over E_alt, B_alt
+    CUtensorMap* ymaps_d = nullptr;      // [2][nboxes][3] plane maps of k_yee_fused: E, B, J of either pair
+    int* fused_off_d = nullptr;
+    int fused_nblocks = 0;
+    int64_t fused_steps = 0;
+    // graphs of a pair of steps, one per frame-table parity of its first step
+    cudaGraph_t pgraph[2] = {nullptr, nullptr};
+    cudaGraphExec_t pgexec[2] = {nullptr, nullptr};
+    cudaGraphNode_t pevnode[2][8] = {};
     // plain form
     std::vector<PlainBox> pboxes;
     // stage timing
@@ -239,6 +254,12 @@ void destroy_graphs(pic_ctx* c)
             cudaGraphDestroy(c->graph[p]);
         c->gexec[p] = nullptr;
         c->graph[p] = nullptr;
+        if (c->pgexec[p])
+            cudaGraphExecDestroy(c->pgexec[p]);
+        if (c->pgraph[p])
+            cudaGraphDestroy(c->pgraph[p]);
+        c->pgexec[p] = nullptr;
+        c->pgraph[p] = nullptr;
     }
 }
 
@@ -341,8 +362,11 @@ pic_status status_check(pic_ctx* c)
 pic_status insert_mixed(pic_ctx* c, int box, int species, int64_t m, const double* sx, const double* su,
                         const double* sw, int id_base, const int64_t* ids);
 pic_status autotune(pic_ctx* c);
+pic_status prepare_fused(pic_ctx* c);
 
-StepDev make_step(const pic_ctx* c, int parity)
+// alt: the step reads its fields from the second buffer pair (the second
+// step of a fused pair)
+StepDev make_step(const pic_ctx* c, int parity, bool alt = false)
 {
     StepDev d{};
     d.LX = c->LX;
@@ -358,8 +382,8 @@ StepDev make_step(const pic_ctx* c, int parity)
     d.dt = (float)c->dt;
     for (int a = 0; a < 3; ++a)
         d.move[a] = (float)(c->dt / c->h[a]);
-    d.boxes = c->boxes_d;
-    d.tmaps = c->tmaps_d;
+    d.boxes = alt ? c->boxes_alt_d : c->boxes_d;
+    d.tmaps = alt ? c->tmaps_alt_d : c->tmaps_d;
     d.sc_box = c->sc_box_d;
     d.items = c->items_d;
     const double V = c->h[0] * c->h[1] * c->h[2];
@@ -532,11 +556,22 @@ YeePlan yee_plan(const pic_ctx* c)
                    c->any_antenna ? 1 : 0, c->guard, c->sub_z ? 1 : 0};
 }
 
-// One stage of the mixed-form step (PIC_STAGE_*) on frame-table parity
-// `parity`; the Yee stages run one part of the field update each.
-pic_status enqueue_stage(pic_ctx* c, int stage, int parity)
+// The fused field update of one step: from the first buffer pair into the
+// second (src 0) or back (src 1).
+FusedPlan fused_plan(const pic_ctx* c, int src)
 {
-    const StepDev d = make_step(c, parity);
+    return FusedPlan{src ? c->boxes_alt_d : c->boxes_d, src ? c->boxes_d : c->boxes_alt_d,
+                     c->ymaps_d + (size_t)src * 3 * c->nboxes, c->fused_off_d, c->fused_nblocks, c->status_d};
+}
+
+// One stage of the mixed-form step (PIC_STAGE_*) on frame-table parity
+// `parity`; the Yee stages run one part of the field update each.  fsrc 0 /
+// 1: a step of a fused pair, whose fields are read from the first / second
+// buffer pair (the push and frames stages only; its field update is
+// launch_yee_fused).
+pic_status enqueue_stage(pic_ctx* c, int stage, int parity, int fsrc = -1)
+{
+    const StepDev d = make_step(c, parity, fsrc == 1);
     switch (stage) {
     case PIC_STAGE_PUSH:
         CK(cudaMemsetAsync(c->work_counter, 0, sizeof(int), c->stream));
@@ -557,21 +592,36 @@ pic_status enqueue_stage(pic_ctx* c, int stage, int parity)
     }
 }
 
-pic_status enqueue_step_mixed(pic_ctx* c, int parity, cudaEvent_t* ev, bool external = false)
+// One step; fsrc -1: in place, 0 / 1: the first / second step of a fused
+// pair (fields read from the first / second buffer pair, written to the
+// other).
+pic_status enqueue_step_mixed(pic_ctx* c, int parity, cudaEvent_t* ev, bool external = false, int fsrc = -1)
 {
     if (ev)
         CK(record(ev[0], c->stream, external));
-    CKS(enqueue_stage(c, PIC_STAGE_PUSH, parity));
+    CKS(enqueue_stage(c, PIC_STAGE_PUSH, parity, fsrc));
     if (ev)
         CK(record(ev[1], c->stream, external));
-    CKS(enqueue_stage(c, PIC_STAGE_FRAMES, parity));
+    CKS(enqueue_stage(c, PIC_STAGE_FRAMES, parity, fsrc));
     if (ev)
         CK(record(ev[2], c->stream, external));
-    for (int st = PIC_STAGE_B_FIRST; st <= PIC_STAGE_B_SECOND; ++st)
-        CKS(enqueue_stage(c, st, parity));
+    if (fsrc >= 0) {
+        CK(launch_yee_fused(yee_plan(c), fused_plan(c, fsrc), c->stream));
+    } else {
+        for (int st = PIC_STAGE_B_FIRST; st <= PIC_STAGE_B_SECOND; ++st)
+            CKS(enqueue_stage(c, st, parity));
+    }
     if (ev)
         CK(record(ev[3], c->stream, external));
     return PIC_OK;
+}
+
+// Two steps with the fused field update: first pair -> second -> first, so
+// that the state is back in the first buffer pair; ev: 8 events (or null).
+pic_status enqueue_pair_mixed(pic_ctx* c, int parity, cudaEvent_t* ev, bool external = false)
+{
+    CKS(enqueue_step_mixed(c, parity, ev, external, 0));
+    return enqueue_step_mixed(c, parity ^ 1, ev ? ev + 4 : nullptr, external, 1);
 }
 
 // Before the first step: room in the frame pool for one step of growth,
@@ -593,6 +643,7 @@ pic_status prepare_mixed(pic_ctx* c)
     int per_sm = 0;
     CK(configure_push(c->LX, c->LY, c->LZ, c->threads, c->guard, &per_sm));
     c->push_grid = std::max(1, per_sm) * c->nsm;
+    CKS(prepare_fused(c));
     c->prepared = true;
     return PIC_OK;
 }
@@ -655,6 +706,70 @@ pic_status capture_graphs(pic_ctx* c)
     return PIC_OK;
 }
 
+// Capture a pair of steps with the fused field update per frame-table
+// parity of its first step (after capture_graphs succeeded).  A failure
+// leaves pairs on eager launches.
+pic_status capture_pair_graphs(pic_ctx* c)
+{
+    if (!c->fused_ready || c->pgexec[0] || c->graph_failed || !c->gexec[0])
+        return PIC_OK;
+    for (int p = 0; p < 2; ++p) {
+        cudaGraph_t g = nullptr;
+        if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            cudaGetLastError();
+            c->graph_failed = true;
+            return PIC_OK;
+        }
+        pic_status st = enqueue_pair_mixed(c, p, c->placeholder, true);
+        cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+        if (st != PIC_OK) {
+            if (g)
+                cudaGraphDestroy(g);
+            return st;
+        }
+        bool ok = e == cudaSuccess && g;
+        int found = 0;
+        if (ok) {
+            size_t n = 0;
+            ok = cudaGraphGetNodes(g, nullptr, &n) == cudaSuccess;
+            std::vector<cudaGraphNode_t> nodes(n);
+            ok = ok && cudaGraphGetNodes(g, nodes.data(), &n) == cudaSuccess;
+            for (size_t i = 0; ok && i < n; ++i) {
+                cudaGraphNodeType t;
+                if (cudaGraphNodeGetType(nodes[i], &t) != cudaSuccess || t != cudaGraphNodeTypeEventRecord)
+                    continue;
+                cudaEvent_t ev = nullptr;
+                if (cudaGraphEventRecordNodeGetEvent(nodes[i], &ev) != cudaSuccess)
+                    continue;
+                for (int k = 0; k < 8; ++k)
+                    if (ev == c->placeholder[k]) {
+                        c->pevnode[p][k] = nodes[i];
+                        ++found;
+                    }
+            }
+        }
+        ok = ok && found == 8 && cudaGraphInstantiate(&c->pgexec[p], g, 0) == cudaSuccess;
+        if (!ok) {
+            cudaGetLastError();
+            if (g)
+                cudaGraphDestroy(g);
+            destroy_graphs(c);
+            c->graph_failed = true;
+            return PIC_OK;
+        }
+        c->pgraph[p] = g;
+    }
+    return PIC_OK;
+}
+
+pic_status launch_pair_graph(pic_ctx* c, int p, cudaEvent_t* ev)
+{
+    for (int k = 0; k < 8; ++k)
+        CK(cudaGraphExecEventRecordNodeSetEvent(c->pgexec[p], c->pevnode[p][k], ev ? ev[k] : c->placeholder[k]));
+    CK(cudaGraphLaunch(c->pgexec[p], c->stream));
+    return PIC_OK;
+}
+
 pic_status launch_graph(pic_ctx* c, int p, cudaEvent_t* ev)
 {
     for (int k = 0; k < 4; ++k)
@@ -687,19 +802,20 @@ pic_status harvest_events(pic_ctx* c)
     return PIC_OK;
 }
 
-pic_status step_events(pic_ctx* c, cudaEvent_t** out)
+// Events for the next `steps` steps (4 each, contiguous).
+pic_status step_events(pic_ctx* c, cudaEvent_t** out, int steps = 1)
 {
     const int64_t kMaxPending = 512;
-    if (c->ev_steps >= kMaxPending)
+    if (c->ev_steps + steps > kMaxPending)
         CKS(harvest_events(c));
-    size_t need = (size_t)(c->ev_steps + 1) * 4;
+    size_t need = (size_t)(c->ev_steps + steps) * 4;
     while (c->events.size() < need) {
         cudaEvent_t e;
         CK(cudaEventCreate(&e));
         c->events.push_back(e);
     }
     *out = &c->events[(size_t)c->ev_steps * 4];
-    c->ev_steps += 1;
+    c->ev_steps += steps;
     return PIC_OK;
 }
 
@@ -806,17 +922,13 @@ int ilog2(int v)
 
 namespace {
 
-// TMA descriptors of the push's E/B tile loads, one per box and field: the
-// padded field array as a 4D tensor (x, y, z, component), box = the tile
-// (row pitch px, ty rows, tz planes, 3 components), so that one load brings
-// a supercell's three components into shared memory.  Reads past the array
-// (the pitch beyond the last tile's edge) come back as zeros.
-pic_status encode_tile_maps(pic_ctx* c)
+using TensorEncode = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+TensorEncode tensor_encoder()
 {
-    using Encode = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-    static Encode encode = [] {
+    static TensorEncode encode = [] {
         void* fn = nullptr;
         cudaDriverEntryPointQueryResult q{};
         if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
@@ -825,33 +937,103 @@ pic_status encode_tile_maps(pic_ctx* c)
             cudaGetLastError();
             fn = nullptr;
         }
-        return reinterpret_cast<Encode>(fn);
+        return reinterpret_cast<TensorEncode>(fn);
     }();
+    return encode;
+}
+
+// One box's padded field array F (three components) as a 4D tensor (x, y,
+// z, component) with the given box extents.  Reads past the array come back
+// as zeros.
+pic_status encode_field_map(pic_ctx* c, CUtensorMap* map, const BoxDev& bd, float* F, int bx, int by, int bz,
+                            int box)
+{
+    TensorEncode encode = tensor_encoder();
     if (!encode)
         return fail(c, PIC_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    const cuuint64_t dims[4] = {(cuuint64_t)bd.px, (cuuint64_t)bd.py, (cuuint64_t)bd.pz, 3};
+    const cuuint64_t strides[3] = {(cuuint64_t)bd.px * 4, (cuuint64_t)bd.px * bd.py * 4,
+                                   (cuuint64_t)padded_cells(bd) * 4};
+    const cuuint32_t ext[4] = {(cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bz, 3};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, F, dims, strides, ext, estr,
+                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS)
+        return fail(c, PIC_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d) for box %d", (int)r, box);
+    return PIC_OK;
+}
+
+// TMA descriptors of the push's E/B tile loads, one per box and field, over
+// the fields of the box table `boxes`: box = the tile (row pitch px, ty
+// rows, tz planes, 3 components), so that one load brings a supercell's
+// three components into shared memory.
+pic_status encode_tile_maps(pic_ctx* c, const std::vector<BoxDev>& boxes, CUtensorMap** out)
+{
     int bpx = 0, bty = 0, btz = 0;
     push_tile_box(c->LX, c->LY, c->LZ, c->guard, &bpx, &bty, &btz);
     std::vector<CUtensorMap> maps((size_t)2 * c->nboxes);
-    for (int b = 0; b < c->nboxes; ++b) {
-        const BoxDev& bd = c->boxes_h[b];
-        const cuuint64_t dims[4] = {(cuuint64_t)bd.px, (cuuint64_t)bd.py, (cuuint64_t)bd.pz, 3};
-        const cuuint64_t strides[3] = {(cuuint64_t)bd.px * 4, (cuuint64_t)bd.px * bd.py * 4,
-                                       (cuuint64_t)padded_cells(bd) * 4};
-        const cuuint32_t box[4] = {(cuuint32_t)bpx, (cuuint32_t)bty, (cuuint32_t)btz, 3};
-        const cuuint32_t estr[4] = {1, 1, 1, 1};
-        for (int f = 0; f < 2; ++f) {
-            const CUresult r = encode(&maps[2 * b + f], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, f == 0 ? bd.E : bd.B,
-                                      dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                                      CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-            if (r != CUDA_SUCCESS)
-                return fail(c, PIC_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d) for box %d", (int)r, b);
-        }
-    }
-    CKS(dalloc(c, &c->tmaps_d, 2 * c->nboxes, false));
-    CK(cudaMemcpyAsync(c->tmaps_d, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice,
+    for (int b = 0; b < c->nboxes; ++b)
+        for (int f = 0; f < 2; ++f)
+            CKS(encode_field_map(c, &maps[2 * b + f], boxes[b], f == 0 ? boxes[b].E : boxes[b].B, bpx, bty,
+                                 btz, b));
+    CKS(dalloc(c, out, 2 * c->nboxes, false));
+    CK(cudaMemcpyAsync(*out, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice,
                        c->stream));
     CK(cudaStreamSynchronize(c->stream));
+    return PIC_OK;
+}
+
+pic_status encode_tile_maps(pic_ctx* c) { return encode_tile_maps(c, c->boxes_h, &c->tmaps_d); }
+
+// The host box table with the fields of the second buffer pair.
+std::vector<BoxDev> alt_boxes(const pic_ctx* c)
+{
+    std::vector<BoxDev> alt = c->boxes_h;
+    for (BoxDev& b : alt) {
+        b.E = c->E_alt + (b.E - c->E_all);
+        b.B = c->B_alt + (b.B - c->B_all);
+    }
+    return alt;
+}
+
+// The second field buffer pair of the fused field update, its box table,
+// its push tile maps and the E plane maps of k_yee_fused over both pairs
+// (pic_options.field_update 0; not for subdomain slabs, which step by
+// stages).
+pic_status prepare_fused(pic_ctx* c)
+{
+    if (c->fused_ready || c->opt.field_update != 0 || c->sub_z || c->precision != PIC_PRECISION_MIXED)
+        return PIC_OK;
+    CKS(dalloc(c, &c->E_alt, c->field_floats));
+    CKS(dalloc(c, &c->B_alt, c->field_floats));
+    const std::vector<BoxDev> alt = alt_boxes(c);
+    CKS(dalloc(c, &c->boxes_alt_d, c->nboxes, false));
+    CK(cudaMemcpyAsync(c->boxes_alt_d, alt.data(), sizeof(BoxDev) * c->nboxes, cudaMemcpyHostToDevice,
+                       c->stream));
+    CKS(encode_tile_maps(c, alt, &c->tmaps_alt_d));
+    std::vector<CUtensorMap> ymaps((size_t)6 * c->nboxes);
+    std::vector<int> off(c->nboxes + 1, 0);
+    for (int b = 0; b < c->nboxes; ++b) {
+        for (int src = 0; src < 2; ++src) {
+            const BoxDev& bd = src ? alt[b] : c->boxes_h[b];
+            float* F[3] = {bd.E, bd.B, bd.J};
+            for (int f = 0; f < 3; ++f)
+                CKS(encode_field_map(c, &ymaps[((size_t)src * c->nboxes + b) * 3 + f], bd, F[f], kFusedEX,
+                                     kFusedTY + 3, 1, b));
+        }
+        off[b + 1] = off[b] + fused_blocks(c->boxes_h[b].nx, c->boxes_h[b].ny, c->boxes_h[b].nz);
+    }
+    CK(configure_yee_fused());
+    CKS(dalloc(c, &c->ymaps_d, 6 * c->nboxes, false));
+    CKS(dalloc(c, &c->fused_off_d, c->nboxes + 1, false));
+    CK(cudaMemcpyAsync(c->ymaps_d, ymaps.data(), sizeof(CUtensorMap) * ymaps.size(), cudaMemcpyHostToDevice,
+                       c->stream));
+    CK(cudaMemcpyAsync(c->fused_off_d, off.data(), sizeof(int) * (c->nboxes + 1), cudaMemcpyHostToDevice,
+                       c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->fused_nblocks = off[c->nboxes];
+    c->fused_ready = true;
     return PIC_OK;
 }
 
@@ -875,6 +1057,11 @@ pic_status upload_boxes(pic_ctx* c)
                        cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemcpyAsync(c->abs_off_d, off.data(), sizeof(int) * (c->nboxes + 1),
                        cudaMemcpyHostToDevice, c->stream));
+    if (c->boxes_alt_d) {
+        const std::vector<BoxDev> alt = alt_boxes(c);
+        CK(cudaMemcpyAsync(c->boxes_alt_d, alt.data(), sizeof(BoxDev) * c->nboxes, cudaMemcpyHostToDevice,
+                           c->stream));
+    }
     CK(cudaStreamSynchronize(c->stream));
     return PIC_OK;
 }
@@ -929,7 +1116,7 @@ pic_status pic_create(const pic_grid* grids, int32_t nboxes, const double dx[3],
     c->rho_bg.assign(nboxes, 0.0);
     c->id_next.assign((size_t)nboxes * nspecies, 0);
     if ((c->precision != PIC_PRECISION_FP64_PLAIN && c->precision != PIC_PRECISION_MIXED) ||
-        o.sort_every < 0) {
+        o.sort_every < 0 || o.field_update < 0 || o.field_update > 1) {
         delete c;
         return PIC_ERR_ARG;
     }
@@ -1402,10 +1589,27 @@ pic_status pic_step_async(pic_ctx* c, int32_t nsteps)
     if (c->tune_pending && nsteps > 0)
         CKS(autotune(c));
     CKS(prepare_mixed(c));
-    if (c->opt.use_graph)
+    if (c->opt.use_graph) {
         CKS(capture_graphs(c));
-    for (int i = 0; i < nsteps; ++i) {
+        if (nsteps >= 2)
+            CKS(capture_pair_graphs(c));
+    }
+    for (int i = 0; i < nsteps;) {
         cudaEvent_t* ev = nullptr;
+        if (c->fused_ready && nsteps - i >= 2) {
+            // a pair with the fused field update: the fields go to the
+            // second buffer pair and back
+            if (c->timing)
+                CKS(step_events(c, &ev, 2));
+            if (c->opt.use_graph && c->pgexec[c->parity])
+                CKS(launch_pair_graph(c, c->parity, ev));
+            else
+                CKS(enqueue_pair_mixed(c, c->parity, ev));
+            c->steps_done += 2;
+            c->fused_steps += 2;
+            i += 2;
+            continue;
+        }
         if (c->timing)
             CKS(step_events(c, &ev));
         if (c->opt.use_graph && c->gexec[c->parity])
@@ -1414,6 +1618,7 @@ pic_status pic_step_async(pic_ctx* c, int32_t nsteps)
             CKS(enqueue_step_mixed(c, c->parity, ev));
         c->parity ^= 1;
         ++c->steps_done;
+        ++i;
     }
     return PIC_OK;
 }
@@ -1910,7 +2115,9 @@ pic_status pic_info(pic_ctx* c, int32_t key, int64_t* out)
             // push; scan reduce, top; apply, place, free; Yee x3; antenna; y absorber;
             // a subdomain slab adds its 16 halo pack/unpack launches (J, B, E, B:
             // two faces each way) and 2 migrant accepts
-            *out = 1 + 2 + 3 + 3 + (c->any_antenna ? 1 : 0) + (c->abs_nblocks > 0 ? 1 : 0) +
+            // (the fused field update: one kernel for the three)
+            const bool fused = c->opt.field_update == 0 && !c->sub_z;
+            *out = 1 + 2 + 3 + (fused ? 1 : 3) + (c->any_antenna ? 1 : 0) + (c->abs_nblocks > 0 ? 1 : 0) +
                    (c->sub_z ? 18 : 0);
         } else {
             int64_t k = 0;
@@ -1937,6 +2144,9 @@ pic_status pic_info(pic_ctx* c, int32_t key, int64_t* out)
     }
     case PIC_INFO_STEPS:
         *out = c->steps_done;
+        return PIC_OK;
+    case PIC_INFO_FUSED_STEPS:
+        *out = c->fused_steps;
         return PIC_OK;
     case PIC_INFO_HOST_DIRECT:
         *out = c->host_direct;

@@ -199,6 +199,29 @@ struct YeePlan {
     int guard;                 // field guard cells below the interior (1 or 2)
     int sub_z;                 // the (single) box is a subdomain slab: J is not folded in z
 };
+// The fused field update (k_yee_fused): output tiles of kFusedTX x kFusedTY
+// cells z-marching through chunks of kFusedTZ planes; its E, B and J planes
+// arrive by tensor loads of kFusedEX x (kFusedTY + 3) cells (x from the
+// tile's x0 - guard, a 16-byte boundary of the padded row), all three
+// components.
+constexpr int kFusedTX = 32, kFusedTY = 8, kFusedTZ = 32, kFusedEX = 36;
+struct FusedPlan {
+    const BoxDev* src;        // device table of the buffers read (E^n, B^n, J)
+    const BoxDev* dst;        // device table of the buffers written (E^{n+1}, B^{n+1})
+    const CUtensorMap* maps;  // device [nboxes][3]: E, B, J plane maps over src's fields
+    const int* blk_off;       // device [nboxes + 1] block offsets
+    int nblocks;
+    unsigned* status;         // ST_TIMEOUT when a tensor-load wait gave up
+};
+// blocks of the fused field update for one box
+int fused_blocks(int nx, int ny, int nz);
+// its dynamic shared memory, and the kernel attribute that allows it (call
+// once, outside stream capture)
+size_t fused_smem_bytes();
+cudaError_t configure_yee_fused();
+// the whole field update of one step from p.src into f.dst: antenna (into J),
+// k_yee_fused, absorber (on dst); p supplies dt, 1/h, the antenna and absorber
+cudaError_t launch_yee_fused(const YeePlan& p, const FusedPlan& f, cudaStream_t st);
 cudaError_t configure_push(int LX, int LY, int LZ, int threads, int guard, int* per_sm);
 // the E/B tile the push stages per supercell: row pitch px (floats), ty rows, tz planes
 void push_tile_box(int LX, int LY, int LZ, int guard, int* px, int* ty, int* tz);

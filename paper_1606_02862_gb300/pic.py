@@ -39,7 +39,8 @@ EXPORTED = ("pic_create", "pic_set_background", "pic_set_boundary", "pic_set_ant
 STAGE_PUSH, STAGE_FRAMES, STAGE_B_FIRST, STAGE_E, STAGE_B_SECOND = range(5)
 (INFO_GRAPH_ACTIVE, INFO_KERNELS_PER_STEP, INFO_POOL_FRAMES, INFO_FRAMES_USED, INFO_MOVE_CAPACITY,
  INFO_STEPS, INFO_HOST_DIRECT, INFO_SUPERCELL_X, INFO_SUPERCELL_Y, INFO_SUPERCELL_Z, INFO_THREADS,
- INFO_TUNE_TRIALS) = range(12)
+ INFO_TUNE_TRIALS, INFO_FUSED_STEPS) = range(13)
+FIELD_UPDATE_FUSED, FIELD_UPDATE_IN_PLACE = 0, 1
 
 
 class PicError(RuntimeError):
@@ -84,6 +85,7 @@ class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("sc", ctypes.c_int32 * 3),
                 ("threads_per_sc", ctypes.c_int32), ("track_ids", ctypes.c_int32),
                 ("use_graph", ctypes.c_int32), ("sort_every", ctypes.c_int32),
+                ("field_update", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("pool_frames", ctypes.c_int64), ("move_capacity", ctypes.c_int64),
                 ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN), ("alloc_ud", ctypes.c_void_p),
                 ("stream", ctypes.c_void_p)]
@@ -193,11 +195,12 @@ class Context:
 
     def __init__(self, grids, dx, dt, species, precision=PRECISION_MIXED, sc=(4, 4, 4),
                  threads_per_sc=None, track_ids=False, use_graph=True, pool_frames=0,
-                 move_capacity=0, torch_memory=True, sort_every=0):
+                 move_capacity=0, torch_memory=True, sort_every=0, field_update=FIELD_UPDATE_FUSED):
         """sc = (0, 0, 0) and/or threads_per_sc = 0 leave the configuration
         to the library's tuner (at the first step); threads_per_sc = None
         takes the supercell's default (256 threads from 256 cells on, else
-        128)."""
+        128); field_update picks the fused two-buffer field update for pairs
+        of steps (the default) or the three in-place kernels on every step."""
         if threads_per_sc is None:
             cells = int(sc[0]) * int(sc[1]) * int(sc[2])
             threads_per_sc = 256 if cells >= 256 else 128
@@ -222,6 +225,7 @@ class Context:
         o.track_ids = int(bool(track_ids))
         o.use_graph = int(bool(use_graph))
         o.sort_every = int(sort_every)
+        o.field_update = int(field_update)
         o.pool_frames = int(pool_frames)
         o.move_capacity = int(move_capacity)
         self._mem = None
