@@ -383,11 +383,13 @@ def run_ours(args, rank, world, dist):
     total_ms = ev0.elapsed_time(ev1)
     stage_ms, nst = ctx.stage_times()
     graph = bool(ctx.info(pic.INFO_GRAPH_ACTIVE))
-    # launches per step with the fused field update (the context's default);
-    # an in-place step (an odd last one) makes two more
+    # launches per step of the field update in use (libpic times the fused
+    # and the in-place form at the first step and keeps the faster); with
+    # the fused one an in-place step (an odd last one) makes two more
     kernels = ctx.info(pic.INFO_KERNELS_PER_STEP)
+    field_update = ctx.info(pic.INFO_FIELD_UPDATE)
     fused_in = ctx.info(pic.INFO_FUSED_STEPS) - fused0
-    launches = kernels * args.steps + 2 * (args.steps - fused_in)
+    launches = kernels * args.steps + (2 * (args.steps - fused_in) if field_update == pic.FIELD_UPDATE_FUSED else 0)
     assert nst == args.steps, (nst, args.steps)
     ctx.stage_timing(False)
     ctx.close()
@@ -407,6 +409,8 @@ def run_ours(args, rank, world, dist):
     tpp = prof["tpp"]
     result.update(value=value, step_ms=step_ms_max, push_ms=push_ms, frames_ms=frames_ms,
                   yee_ms=yee_ms, graph=graph, kernels=kernels, launches=launches, achieved=achieved,
+                  field_update="fused two-buffer kernel" if field_update == pic.FIELD_UPDATE_FUSED
+                  else "three in-place kernels",
                   traffic=None if tpp is None else tpp * npart, clocks=clk.summary(), wpp=prof["wpp"],
                   wkind=prof["wkind"],
                   fpp=prof["fpp"])
@@ -481,6 +485,7 @@ def run_ours(args, rank, world, dist):
                            f"{args.threads} threads/supercell"
                            + (f" (tuned by libpic over {tune_trials} configurations)" if tune_trials else ""),
                    "graph": result["graph"],
+                   "field_update": result["field_update"],
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "inputs larger than L2 (particles 4.3 GB/GPU)"},
         "push_deposit_ms_per_step": result["push_ms"] + result["frames_ms"],
@@ -686,6 +691,7 @@ def workload_leg(name, steps, warmup, sc=(8, 4, 4), threads=256, plain_steps=0, 
     else:
         ctx.step(steps)
     ms, nst = ctx.stage_times()
+    fused = ctx.info(pic.INFO_FIELD_UPDATE) == pic.FIELD_UPDATE_FUSED
     ctx.close()
     out = {"workload": f"{name}: {WORKLOADS[name]}", "particles": npart, "cells": ncell, "steps": nst,
            "warmup": warmup, "value": npart / ((ms[0] + ms[1]) / nst * 1e-3), "unit": UNIT,
@@ -695,7 +701,8 @@ def workload_leg(name, steps, warmup, sc=(8, 4, 4), threads=256, plain_steps=0, 
            "step_ms": ms[3] / nst,
            "hbm_frac": (npart * MIXED_BYTES_PER_PARTICLE + ncell * MIXED_BYTES_PER_CELL)
            / (ms[0] / nst * 1e-3) / 1e9 / measured_hbm()[0],
-           "form": f"mixed, supercell {'x'.join(map(str, sc))}, {threads} threads"}
+           "form": f"mixed, supercell {'x'.join(map(str, sc))}, {threads} threads, "
+                   + ("fused two-buffer field update" if fused else "in-place field update")}
     if diags:
         out["diagnostics"] = {"columns": ["step", "field_energy", "kinetic_energy", "charge",
                                           "max_abs_divE_minus_rho"], "rows": diags}

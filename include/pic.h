@@ -95,6 +95,31 @@ enum {
 enum { PIC_FIELD_E = 0, PIC_FIELD_B = 1, PIC_FIELD_J = 2, PIC_FIELD_RHO = 3 };
 
 /*
+ * The field update of the mixed form (pic_options.field_update; Sec. 4: the
+ * Yee solver's half step of B, step of E, half step of B):
+ *   PIC_FIELD_UPDATE_IN_PLACE  three kernels per step (B half, E, B half),
+ *                              each in place: 120 bytes of HBM traffic per cell;
+ *   PIC_FIELD_UPDATE_FUSED     within pic_step calls of two or more steps,
+ *                              one kernel per step that reads E, B, J from
+ *                              one buffer pair and writes E, B into a second
+ *                              one (24 bytes per padded cell, allocated at
+ *                              the first step): 60 bytes per cell.  A pair of
+ *                              steps goes first pair -> second -> first, so
+ *                              between calls the state is in the first pair;
+ *                              an odd last step, and every pic_step_stage,
+ *                              uses the in-place kernels;
+ *   PIC_FIELD_UPDATE_AUTO      (0) at the first step the library times one
+ *                              update of each form on the context's own
+ *                              fields (the fused one writes only the second
+ *                              pair, the in-place one runs on a copy there)
+ *                              and keeps the faster; the second pair is
+ *                              freed if the in-place form wins.
+ * Both forms give the same fields up to FP32 rounding of the same
+ * operations.  pic_info(PIC_INFO_FIELD_UPDATE) reports the form in use.
+ */
+enum { PIC_FIELD_UPDATE_AUTO = 0, PIC_FIELD_UPDATE_IN_PLACE = 1, PIC_FIELD_UPDATE_FUSED = 2 };
+
+/*
  * Supercell shape and threads per supercell (mixed form; Sec. 2.1: a
  * supercell is the unit a block of threads works on, and its shape is a
  * tuning parameter of the code).  Left 0, they are tuned by the library:
@@ -119,16 +144,8 @@ typedef struct {
                                list by nearest node (TSC) / cell (CIC, PCS) and writes it back in that
                                order; the steps between push the lists in stored order; 0 = 4,
                                1 = sort on every step (results agree up to FP32 summation order) */
-    int32_t field_update;   /* mixed form, the field half of the step (Sec. 4, Yee solver):
-                               0 = a pic_step of two or more steps updates the fields of each pair
-                               of steps with one fused kernel per step that reads E, B, J from one
-                               buffer pair and writes E, B into a second one (allocated at the
-                               first step: 24 bytes per padded cell), so that the state is back in
-                               the first pair after every second step; an odd last step, and every
-                               pic_step_stage, uses the three in-place kernels;
-                               1 = the three in-place kernels (B half, E, B half) on every step,
-                               no second buffer pair.  Both give the same fields up to FP32
-                               rounding of the same operations. */
+    int32_t field_update;   /* mixed form, the field half of the step (Sec. 4, Yee solver), one of
+                               PIC_FIELD_UPDATE_* (below); 0 = chosen at the first step */
     int32_t reserved;       /* 0 */
     int64_t pool_frames;    /* frame-pool capacity (mixed); 0 = sized at the first step from the load */
     int64_t move_capacity;  /* capacity of the per-step buffer of particles changing supercell; 0 = auto */
@@ -348,9 +365,12 @@ pic_status pic_stage_times(pic_ctx* ctx, double ms[4], int64_t* nsteps_out);
  *   PIC_INFO_TUNE_TRIALS     configurations the tuner timed for this context (0: given in
  *                            the options, or taken from an earlier tuning in this process);
  *   PIC_INFO_FUSED_STEPS     steps since pic_create whose field update was the fused
- *                            two-buffer kernel (pic_options.field_update 0).
+ *                            two-buffer kernel;
+ *   PIC_INFO_FIELD_UPDATE    the field update in use: PIC_FIELD_UPDATE_IN_PLACE or
+ *                            PIC_FIELD_UPDATE_FUSED (PIC_FIELD_UPDATE_AUTO before the first step
+ *                            of an auto context).
  * PIC_INFO_KERNELS_PER_STEP counts a step of a pic_step of two or more steps (with the
- * fused field update when it is on: two launches fewer than the in-place kernels).
+ * fused field update when it is in use: two launches fewer than the in-place kernels).
  */
 enum {
     PIC_INFO_GRAPH_ACTIVE = 0,
@@ -365,7 +385,8 @@ enum {
     PIC_INFO_SUPERCELL_Z = 9,
     PIC_INFO_THREADS = 10,
     PIC_INFO_TUNE_TRIALS = 11,
-    PIC_INFO_FUSED_STEPS = 12
+    PIC_INFO_FUSED_STEPS = 12,
+    PIC_INFO_FIELD_UPDATE = 13
 };
 pic_status pic_info(pic_ctx* ctx, int32_t key, int64_t* out);
 

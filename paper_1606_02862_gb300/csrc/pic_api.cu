@@ -135,7 +135,8 @@ struct pic_ctx {
     // fused field update (pic_options.field_update 0): a second field buffer
     // pair; a pair of steps goes first -> second -> first.  The tables, push
     // maps and Yee maps of the second pair mirror those of the first.
-    bool fused_ready = false;
+    bool fused_ready = false;   // pairs of steps take the fused update
+    bool field_chosen = false;  // the field update was chosen (at the first step)
     float *E_alt = nullptr, *B_alt = nullptr;
     BoxDev* boxes_alt_d = nullptr;
     CUtensorMap* tmaps_alt_d = nullptr;  // [nboxes][2] push tile maps over E_alt, B_alt
@@ -363,6 +364,8 @@ pic_status insert_mixed(pic_ctx* c, int box, int species, int64_t m, const doubl
                         const double* sw, int id_base, const int64_t* ids);
 pic_status autotune(pic_ctx* c);
 pic_status prepare_fused(pic_ctx* c);
+pic_status choose_field_update(pic_ctx* c);
+pic_status status_check(pic_ctx* c);
 
 // alt: the step reads its fields from the second buffer pair (the second
 // step of a fused pair)
@@ -1003,7 +1006,8 @@ std::vector<BoxDev> alt_boxes(const pic_ctx* c)
 // stages).
 pic_status prepare_fused(pic_ctx* c)
 {
-    if (c->fused_ready || c->opt.field_update != 0 || c->sub_z || c->precision != PIC_PRECISION_MIXED)
+    if (c->fused_ready || c->field_chosen || c->opt.field_update == PIC_FIELD_UPDATE_IN_PLACE || c->sub_z ||
+        c->precision != PIC_PRECISION_MIXED)
         return PIC_OK;
     CKS(dalloc(c, &c->E_alt, c->field_floats));
     CKS(dalloc(c, &c->B_alt, c->field_floats));
@@ -1034,6 +1038,59 @@ pic_status prepare_fused(pic_ctx* c)
     CK(cudaStreamSynchronize(c->stream));
     c->fused_nblocks = off[c->nboxes];
     c->fused_ready = true;
+    c->field_chosen = true;
+    if (c->opt.field_update == PIC_FIELD_UPDATE_AUTO)
+        CKS(choose_field_update(c));
+    return PIC_OK;
+}
+
+// PIC_FIELD_UPDATE_AUTO: one fused update (first pair -> second, which
+// leaves the state alone) against the in-place kernels run on a copy of the
+// fields in the second pair, three times each after a first run of each; the
+// faster by its best time stays.  Only J is written besides the second pair
+// (an antenna adds into it), and the next push zeroes J first.
+pic_status choose_field_update(pic_ctx* c)
+{
+    YeePlan onto_alt = yee_plan(c);
+    onto_alt.boxes = c->boxes_alt_d;
+    const FusedPlan f = fused_plan(c, 0);
+    cudaEvent_t ev[4];
+    for (cudaEvent_t& e : ev)
+        CK(cudaEventCreate(&e));
+    float best_fused = 1e30f, best_in_place = 1e30f;
+    cudaError_t err = cudaSuccess;
+    for (int rep = 0; rep < 4 && err == cudaSuccess; ++rep) {
+        const size_t bytes = sizeof(float) * c->field_floats;
+        if ((err = cudaEventRecord(ev[0], c->stream)) != cudaSuccess ||
+            (err = launch_yee_fused(yee_plan(c), f, c->stream)) != cudaSuccess ||
+            (err = cudaEventRecord(ev[1], c->stream)) != cudaSuccess ||
+            (err = cudaMemcpyAsync(c->E_alt, c->E_all, bytes, cudaMemcpyDeviceToDevice, c->stream)) != cudaSuccess ||
+            (err = cudaMemcpyAsync(c->B_alt, c->B_all, bytes, cudaMemcpyDeviceToDevice, c->stream)) != cudaSuccess ||
+            (err = cudaEventRecord(ev[2], c->stream)) != cudaSuccess ||
+            (err = launch_yee_mixed_plan(onto_alt, c->stream)) != cudaSuccess ||
+            (err = cudaEventRecord(ev[3], c->stream)) != cudaSuccess ||
+            (err = cudaStreamSynchronize(c->stream)) != cudaSuccess)
+            break;
+        float tf = 0, ti = 0;
+        if ((err = cudaEventElapsedTime(&tf, ev[0], ev[1])) != cudaSuccess ||
+            (err = cudaEventElapsedTime(&ti, ev[2], ev[3])) != cudaSuccess)
+            break;
+        if (rep > 0) {
+            best_fused = std::min(best_fused, tf);
+            best_in_place = std::min(best_in_place, ti);
+        }
+    }
+    for (cudaEvent_t e : ev)
+        cudaEventDestroy(e);
+    CK(err);
+    CKS(status_check(c));
+    if (best_fused < best_in_place)
+        return PIC_OK;
+    // the in-place kernels: drop the second pair
+    c->fused_ready = false;
+    raw_free(c, c->E_alt);
+    raw_free(c, c->B_alt);
+    c->E_alt = c->B_alt = nullptr;
     return PIC_OK;
 }
 
@@ -1116,7 +1173,7 @@ pic_status pic_create(const pic_grid* grids, int32_t nboxes, const double dx[3],
     c->rho_bg.assign(nboxes, 0.0);
     c->id_next.assign((size_t)nboxes * nspecies, 0);
     if ((c->precision != PIC_PRECISION_FP64_PLAIN && c->precision != PIC_PRECISION_MIXED) ||
-        o.sort_every < 0 || o.field_update < 0 || o.field_update > 1) {
+        o.sort_every < 0 || o.field_update < PIC_FIELD_UPDATE_AUTO || o.field_update > PIC_FIELD_UPDATE_FUSED) {
         delete c;
         return PIC_ERR_ARG;
     }
@@ -2116,7 +2173,7 @@ pic_status pic_info(pic_ctx* c, int32_t key, int64_t* out)
             // a subdomain slab adds its 16 halo pack/unpack launches (J, B, E, B:
             // two faces each way) and 2 migrant accepts
             // (the fused field update: one kernel for the three)
-            const bool fused = c->opt.field_update == 0 && !c->sub_z;
+            const bool fused = c->fused_ready;
             *out = 1 + 2 + 3 + (fused ? 1 : 3) + (c->any_antenna ? 1 : 0) + (c->abs_nblocks > 0 ? 1 : 0) +
                    (c->sub_z ? 18 : 0);
         } else {
@@ -2147,6 +2204,12 @@ pic_status pic_info(pic_ctx* c, int32_t key, int64_t* out)
         return PIC_OK;
     case PIC_INFO_FUSED_STEPS:
         *out = c->fused_steps;
+        return PIC_OK;
+    case PIC_INFO_FIELD_UPDATE:
+        *out = c->fused_ready ? PIC_FIELD_UPDATE_FUSED
+                              : (c->field_chosen || c->opt.field_update == PIC_FIELD_UPDATE_IN_PLACE || c->sub_z
+                                     ? PIC_FIELD_UPDATE_IN_PLACE
+                                     : PIC_FIELD_UPDATE_AUTO);
         return PIC_OK;
     case PIC_INFO_HOST_DIRECT:
         *out = c->host_direct;

@@ -39,8 +39,8 @@ EXPORTED = ("pic_create", "pic_set_background", "pic_set_boundary", "pic_set_ant
 STAGE_PUSH, STAGE_FRAMES, STAGE_B_FIRST, STAGE_E, STAGE_B_SECOND = range(5)
 (INFO_GRAPH_ACTIVE, INFO_KERNELS_PER_STEP, INFO_POOL_FRAMES, INFO_FRAMES_USED, INFO_MOVE_CAPACITY,
  INFO_STEPS, INFO_HOST_DIRECT, INFO_SUPERCELL_X, INFO_SUPERCELL_Y, INFO_SUPERCELL_Z, INFO_THREADS,
- INFO_TUNE_TRIALS, INFO_FUSED_STEPS) = range(13)
-FIELD_UPDATE_FUSED, FIELD_UPDATE_IN_PLACE = 0, 1
+ INFO_TUNE_TRIALS, INFO_FUSED_STEPS, INFO_FIELD_UPDATE) = range(14)
+FIELD_UPDATE_AUTO, FIELD_UPDATE_IN_PLACE, FIELD_UPDATE_FUSED = 0, 1, 2
 
 
 class PicError(RuntimeError):
@@ -195,12 +195,13 @@ class Context:
 
     def __init__(self, grids, dx, dt, species, precision=PRECISION_MIXED, sc=(4, 4, 4),
                  threads_per_sc=None, track_ids=False, use_graph=True, pool_frames=0,
-                 move_capacity=0, torch_memory=True, sort_every=0, field_update=FIELD_UPDATE_FUSED):
+                 move_capacity=0, torch_memory=True, sort_every=0, field_update=FIELD_UPDATE_AUTO):
         """sc = (0, 0, 0) and/or threads_per_sc = 0 leave the configuration
         to the library's tuner (at the first step); threads_per_sc = None
         takes the supercell's default (256 threads from 256 cells on, else
-        128); field_update picks the fused two-buffer field update for pairs
-        of steps (the default) or the three in-place kernels on every step."""
+        128); field_update picks the field update: the three in-place kernels,
+        the fused two-buffer kernel for pairs of steps, or (the default) the
+        faster of the two on this context's fields, timed at the first step."""
         if threads_per_sc is None:
             cells = int(sc[0]) * int(sc[1]) * int(sc[2])
             threads_per_sc = 256 if cells >= 256 else 128

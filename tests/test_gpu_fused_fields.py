@@ -14,8 +14,11 @@ Checked:
     an open-y box with absorber and antenna;
   * against the FP64 oracle over one fused pair from a read-back state (the
     per-step tolerance of the other parity tests, twice);
-  * PIC_INFO_FUSED_STEPS counts the fused steps: an odd last step and
-    field_update 1 take the in-place kernels.
+  * PIC_INFO_FUSED_STEPS counts the fused steps: an odd last step and the
+    in-place form take the in-place kernels;
+  * the automatic choice (field_update 0) settles on one form at the first
+    step, reports it, and follows the forced in-place form within the
+    parity tolerance.
 """
 import numpy as np
 import pytest
@@ -148,7 +151,8 @@ def test_fused_graph_and_eager_agree():
     wl = _workload("uneven", seed=2)
     outs = []
     for use_graph in (True, False):
-        ctx = ctx_from(wl, sc=(8, 4, 4), threads_per_sc=128, use_graph=use_graph)
+        ctx = ctx_from(wl, sc=(8, 4, 4), threads_per_sc=128, use_graph=use_graph,
+                       field_update=pic.FIELD_UPDATE_FUSED)
         try:
             ctx.step(4)
             assert ctx.info(pic.INFO_FUSED_STEPS) == 4
@@ -156,3 +160,25 @@ def test_fused_graph_and_eager_agree():
         finally:
             ctx.close()
     _agree(outs[0], outs[1], wl, TOL_J)
+
+
+def test_automatic_choice_settles_on_one_form():
+    require_gpu()
+    from paper_1606_02862_gb300 import pic
+
+    wl = _workload("uneven", seed=3)
+    auto = ctx_from(wl, sc=(8, 4, 4), threads_per_sc=128)
+    ref = _ctx(wl, "uneven", pic.FIELD_UPDATE_IN_PLACE)
+    try:
+        assert auto.info(pic.INFO_FIELD_UPDATE) == pic.FIELD_UPDATE_AUTO
+        auto.step(4)
+        ref.step(4)
+        form = auto.info(pic.INFO_FIELD_UPDATE)
+        assert form in (pic.FIELD_UPDATE_IN_PLACE, pic.FIELD_UPDATE_FUSED)
+        assert auto.info(pic.INFO_FUSED_STEPS) == (4 if form == pic.FIELD_UPDATE_FUSED else 0)
+        assert ref.info(pic.INFO_FIELD_UPDATE) == pic.FIELD_UPDATE_IN_PLACE
+        print("automatic choice:", "fused" if form == pic.FIELD_UPDATE_FUSED else "in place",
+              _agree(_state(auto, wl), _state(ref, wl), wl, TOL_J))
+    finally:
+        auto.close()
+        ref.close()
