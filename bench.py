@@ -755,7 +755,7 @@ def run_workload(args):
 def run_yee(args):
     """The field update alone (scope row a5): an n^3 box without particles,
     random E, stage events around the field update of each step.  The
-    default form is the fused two-buffer kernel (pic_options.field_update 0:
+    headline form is the fused two-buffer kernel (PIC_FIELD_UPDATE_FUSED:
     one kernel per step, pairs of steps, so the step count is rounded up to
     an even number); the three in-place kernels (B half, E, B half) are timed
     beside it.  Rate in cell updates/s; roofline against the algorithmic 60

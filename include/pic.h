@@ -145,7 +145,7 @@ typedef struct {
                                order; the steps between push the lists in stored order; 0 = 4,
                                1 = sort on every step (results agree up to FP32 summation order) */
     int32_t field_update;   /* mixed form, the field half of the step (Sec. 4, Yee solver), one of
-                               PIC_FIELD_UPDATE_* (below); 0 = chosen at the first step */
+                               PIC_FIELD_UPDATE_* (above); 0 = chosen at the first step */
     int32_t reserved;       /* 0 */
     int64_t pool_frames;    /* frame-pool capacity (mixed); 0 = sized at the first step from the load */
     int64_t move_capacity;  /* capacity of the per-step buffer of particles changing supercell; 0 = auto */

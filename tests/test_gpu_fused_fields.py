@@ -1,9 +1,11 @@
-"""The fused two-buffer field update (pic_options.field_update 0) through the
-C ABI.  A pic_step of two or more steps updates the fields of each pair of
-steps with k_yee_fused: E^n, B^n, J read from one buffer pair, E^{n+1},
+"""The fused two-buffer field update (pic_options.field_update
+PIC_FIELD_UPDATE_FUSED, or chosen by the automatic mode) through the C ABI.
+A pic_step of two or more steps updates the fields of each pair of steps
+with k_yee_fused: E^n, B^n, J read from one buffer pair, E^{n+1},
 B^{n+1} written to the other, and back on the second step of the pair.
 Checked:
-  * against the three in-place kernels (field_update 1) from the same state:
+  * against the three in-place kernels (PIC_FIELD_UPDATE_IN_PLACE) from the
+    same state:
     after the first pair E, B and every particle agree to FP32 rounding (rel
     1e-6 of the max norm, 1e-6 cells); J, whose fixed-point chunk sums round
     each term to 2^-21 of the chunk's largest and whose global sums run in
@@ -16,8 +18,8 @@ Checked:
     per-step tolerance of the other parity tests, twice);
   * PIC_INFO_FUSED_STEPS counts the fused steps: an odd last step and the
     in-place form take the in-place kernels;
-  * the automatic choice (field_update 0) settles on one form at the first
-    step, reports it, and follows the forced in-place form within the
+  * the automatic choice (PIC_FIELD_UPDATE_AUTO, 0) settles on one form at
+    the first step, reports it, and follows the forced in-place form within the
     parity tolerance.
 """
 import numpy as np
