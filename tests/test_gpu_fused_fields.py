@@ -184,3 +184,21 @@ def test_automatic_choice_settles_on_one_form():
     finally:
         auto.close()
         ref.close()
+
+
+def test_field_update_option_is_checked():
+    require_gpu()
+    from paper_1606_02862_gb300 import pic
+    from paper_1606_02862_gb300 import workloads as W
+
+    with pytest.raises(pic.PicError):
+        pic.Context([(16, 16, 16)], (1.0, 1.0, 1.0), W.DT_HALF_COURANT, [pic.Species(-1.0, 1.0, 2)],
+                    sc=(4, 4, 4), field_update=3)
+    # a subdomain slab steps by stages: its field update is the in-place one
+    ctx = pic.Context([(16, 16, 16)], (1.0, 1.0, 1.0), W.DT_HALF_COURANT, [pic.Species(-1.0, 1.0, 2)],
+                      sc=(4, 4, 4), field_update=pic.FIELD_UPDATE_FUSED, use_graph=False)
+    try:
+        ctx.set_subdomain(True)
+        assert ctx.info(pic.INFO_FIELD_UPDATE) == pic.FIELD_UPDATE_IN_PLACE
+    finally:
+        ctx.close()
