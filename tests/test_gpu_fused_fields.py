@@ -202,3 +202,24 @@ def test_field_update_option_is_checked():
         assert ctx.info(pic.INFO_FIELD_UPDATE) == pic.FIELD_UPDATE_IN_PLACE
     finally:
         ctx.close()
+
+
+def test_fused_pairs_across_a_window_shift():
+    """The moving window shifts the first buffer pair between pic_step calls;
+    the fused pairs then continue from it."""
+    require_gpu()
+    from paper_1606_02862_gb300 import pic
+
+    wl = _workload("open_y", seed=4)
+    fused, in_place = _ctx(wl, "open_y", pic.FIELD_UPDATE_FUSED), _ctx(wl, "open_y", pic.FIELD_UPDATE_IN_PLACE)
+    try:
+        for c in (fused, in_place):
+            c.step(2)
+            c.shift_window(0, 4)
+            c.step(4)
+        errs = _agree(_state(fused, wl), _state(in_place, wl), wl, TOL_J)
+        print("window shift:", errs)
+        assert fused.info(pic.INFO_FUSED_STEPS) == 6
+    finally:
+        fused.close()
+        in_place.close()
