@@ -204,7 +204,7 @@ struct YeePlan {
 // arrive by tensor loads of kFusedEX x (kFusedTY + 3) cells (x from the
 // tile's x0 - guard, a 16-byte boundary of the padded row), all three
 // components.
-constexpr int kFusedTX = 32, kFusedTY = 8, kFusedTZ = 32, kFusedEX = 36;
+constexpr int kFusedTX = 32, kFusedTY = 8, kFusedTZ = 24, kFusedEX = 36;
 struct FusedPlan {
     const BoxDev* src;        // device table of the buffers read (E^n, B^n, J)
     const BoxDev* dst;        // device table of the buffers written (E^{n+1}, B^{n+1})

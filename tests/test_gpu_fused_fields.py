@@ -48,7 +48,7 @@ def _workload(kind, seed=0):
     from paper_1606_02862_gb300 import workloads as W
 
     rng = np.random.default_rng(7000 + seed)
-    if kind == "uneven":  # x tiles of 32 + 16, y tiles of 8, z chunks of 32 + 8; a second box
+    if kind == "uneven":  # x tiles of 32 + 16, y tiles of 8, z chunks of 24 + 16; a second box
         boxes, shape = [_box(rng, 48, 24, 40), _box(rng, 32, 16, 16)], 2
     elif kind == "pcs":  # guard layout 2
         boxes, shape = [_box(rng, 32, 16, 16)], 3
